@@ -1,0 +1,416 @@
+"""Pins of the oracle's RNG, Metropolis table and Potts sweep (CPU only).
+
+Each test checks the oracle against something other than itself: a library
+implementation, exact enumeration of transition probabilities from the global
+Hamiltonian, closed forms, or invariants the paper states.
+"""
+import itertools
+import json
+import math
+import os
+import subprocess
+import sys
+from collections import defaultdict
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_1007_3509_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# --------------------------------------------------------------------------
+# Philox4x32-10
+# --------------------------------------------------------------------------
+_TRITON_SNIPPET = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def k(seed, c0p, c1p, c2p, c3p, o0, o1, o2, o3, N: tl.constexpr):
+    offs = tl.arange(0, N)
+    c0 = tl.load(c0p + offs); c1 = tl.load(c1p + offs); c2 = tl.load(c2p + offs); c3 = tl.load(c3p + offs)
+    r0, r1, r2, r3 = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(o0 + offs, r0); tl.store(o1 + offs, r1); tl.store(o2 + offs, r2); tl.store(o3 + offs, r3)
+
+req = json.loads(sys.stdin.read())
+ctr = np.array(req["ctr"], dtype=np.uint32).reshape(-1, 4)
+N = ctr.shape[0]
+c = [torch.from_numpy(ctr[:, i].view(np.int32).copy()) for i in range(4)]
+o = [torch.zeros(N, dtype=torch.int32) for _ in range(4)]
+k[(1,)](req["seed"], *c, *o, N=N)
+print(json.dumps([x.numpy().view(np.uint32).tolist() for x in o]))
+"""
+
+
+def test_philox_matches_triton_library(oracle):
+    """Philox4x32-10 of the oracle equals triton's library Philox (run on CPU by its interpreter)."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2**32, size=(64, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = [0xFFFFFFFF] * 4
+    for seed in (0, 1, 0x0123456789ABCDEF, 2**64 - 1):
+        env = dict(os.environ, TRITON_INTERPRET="1")
+        res = subprocess.run([sys.executable, "-c", _TRITON_SNIPPET], input=json.dumps(
+            {"seed": int(seed), "ctr": ctr.ravel().tolist()}), capture_output=True, text=True, env=env, timeout=600)
+        if res.returncode != 0:
+            pytest.skip(f"triton interpreter unavailable: {res.stderr[-300:]}")
+        lib_out = np.array(json.loads(res.stdout.strip().splitlines()[-1]), dtype=np.uint64).T.astype(np.uint32)
+        ours = oracle.philox(seed, ctr)
+        np.testing.assert_array_equal(ours, lib_out)
+
+
+def test_philox_uniform_and_avalanche(oracle):
+    n = 1 << 18
+    ctr = oracle.counters(np.arange(n), 3, oracle.TAG_SWEEP, 1)
+    out = oracle.philox(12345, ctr)
+    for w in range(4):
+        h, _ = np.histogram(out[:, w] >> 24, bins=256, range=(0, 256))
+        assert stats.chisquare(h).pvalue > 1e-4
+    # flipping one counter bit flips about half of the output bits
+    ctr2 = ctr.copy()
+    ctr2[:, 2] ^= np.uint32(1)
+    out2 = oracle.philox(12345, ctr2)
+    flips = np.unpackbits((out ^ out2).view(np.uint8)).mean()
+    assert abs(flips - 0.5) < 0.002
+    # serial correlation of consecutive draws
+    u = out[:, 0].astype(np.float64)
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 0.01
+
+
+# --------------------------------------------------------------------------
+# Metropolis threshold table
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kT", [0.3, 0.5, 0.7, 0.9, 2.6])
+def test_threshold_table_geometric(oracle, kT):
+    thr, D = oracle.threshold_table(kT)
+    assert thr[0] == 0xFFFFFFFF
+    t = thr[1:].astype(np.float64)
+    assert np.all(np.diff(t) <= 0) and t[-1] >= 1
+    # successive ratios equal exp(-1/(256 kT)) up to the floor (geometric sequence)
+    r = math.exp(-1.0 / (256.0 * kT))
+    big = t > 2**20
+    assert np.allclose(t[1:][big[1:]] / t[:-1][big[1:]], r, rtol=2e-6)
+    # the next entry after D would be below one in 2^32
+    assert 2**32 * math.exp(-(D + 1) / (256.0 * kT)) < 1.0 <= 2**32 * math.exp(-D / (256.0 * kT))
+    thr_s, D_s = oracle.threshold_table(kT, zero_rule=1)
+    assert thr_s[0] == 0 and D_s == D and np.array_equal(thr_s[1:], thr[1:])
+
+
+def test_threshold_table_zero_temperature(oracle):
+    thr, D = oracle.threshold_table(0.0)
+    assert D == 0 and thr[0] == 0xFFFFFFFF
+
+
+# --------------------------------------------------------------------------
+# Potts sweep: exact one-MCS marginals from the global Hamiltonian
+# --------------------------------------------------------------------------
+def _coords(L):
+    if len(L) == 2:
+        return [(x, y, 0) for y in range(L[1]) for x in range(L[0])]
+    return [(x, y, z) for z in range(L[2]) for y in range(L[1]) for x in range(L[0])]
+
+
+def _neighbour_sets(L, nbr):
+    """Neighbour set of every site by its metric definition (no ordering)."""
+    dim = len(L)
+    Lz = L[2] if dim == 3 else 1
+    rng = [-1, 0, 1]
+    offs = []
+    for dz in (rng if dim == 3 else [0]):
+        for dy in rng:
+            for dx in rng:
+                if (dx, dy, dz) == (0, 0, 0):
+                    continue
+                l1 = abs(dx) + abs(dy) + abs(dz)
+                if nbr in (4, 6) and l1 != 1:
+                    continue
+                offs.append((dx, dy, dz))
+    assert len(offs) == nbr
+    sets = []
+    for (x, y, z) in _coords(L):
+        s = []
+        for dx, dy, dz in offs:
+            s.append(((x + dx) % L[0]) + L[0] * (((y + dy) % L[1]) + L[1] * ((z + dz) % Lz)))
+        sets.append(s)
+    return sets
+
+
+def _colour(L, nbr, i):
+    x, y, z = _coords(L)[i]
+    if nbr in (4, 6):
+        return (x + y + z) % 2
+    if len(L) == 2:
+        return (x % 2) + 2 * (y % 2)
+    return (x % 2) + 2 * (y % 2) + 4 * (z % 2)
+
+
+def _bonds(nsets):
+    bonds = set()
+    for i, s in enumerate(nsets):
+        for j in s:
+            bonds.add((min(i, j), max(i, j)))
+    return sorted(bonds)
+
+
+def _energy(conf, bonds, J_fix, bgrain):
+    """H of Eq. (7) with J (1 - delta) per bond counted once, plus sum_i b(q_i) (fixed point)."""
+    e = sum(J_fix for (i, j) in bonds if conf[i] != conf[j])
+    return e + sum(int(bgrain[s]) for s in conf)
+
+
+def _p_accept(d, thr, D):
+    if d < 0:
+        return 1.0
+    if d > D:
+        return 0.0
+    return 1.0 if thr[d] == 0xFFFFFFFF else thr[d] / 2.0**32
+
+
+def _site_transition(conf, i, nsets, bonds, J_fix, bgrain, thr, D):
+    e0 = _energy(conf, bonds, J_fix, bgrain)
+    M = len(nsets[i])
+    out = defaultdict(float)
+    for j in nsets[i]:
+        s = conf[j]
+        if s == conf[i]:
+            out[s] += 1.0 / M
+            continue
+        c2 = list(conf)
+        c2[i] = s
+        d = _energy(c2, bonds, J_fix, bgrain) - e0
+        p = _p_accept(d, thr, D)
+        out[s] += p / M
+        out[conf[i]] += (1.0 - p) / M
+    return out
+
+
+def exact_marginals(q0, L, nbr, J_fix, bgrain, thr, D, phases):
+    """Exact per-site distribution after `phases` colour phases of one MCS."""
+    nsets = _neighbour_sets(L, nbr)
+    bonds = _bonds(nsets)
+    N = len(q0)
+    C = {4: 2, 6: 2, 8: 4, 26: 8}[nbr]
+    marg = [None] * N
+    dist = {tuple(int(v) for v in q0): 1.0}
+    for c in range(min(phases, C)):
+        sites = [i for i in range(N) if _colour(L, nbr, i) == c]
+        last = c == min(phases, C) - 1
+        new = defaultdict(float)
+        acc = {i: defaultdict(float) for i in sites}
+        for conf, p in dist.items():
+            trans = [_site_transition(conf, i, nsets, bonds, J_fix, bgrain, thr, D) for i in sites]
+            for i, t in zip(sites, trans):
+                for s, ps in t.items():
+                    acc[i][s] += p * ps
+            if not last:
+                for combo in itertools.product(*[list(t.items()) for t in trans]):
+                    c2 = list(conf)
+                    pp = p
+                    for i, (s, ps) in zip(sites, combo):
+                        c2[i] = s
+                        pp *= ps
+                    if pp > 0:
+                        new[tuple(c2)] += pp
+        for i in sites:
+            marg[i] = dict(acc[i])
+        if not last:
+            dist = new
+    return marg
+
+
+def _empirical(oracle, q0, L, nbr, J_fix, bfield, thr, D, seeds):
+    dim = len(L)
+    res = np.empty((len(seeds), len(q0)), dtype=np.int32)
+    for k, s in enumerate(seeds):
+        b = bfield[q0] if bfield is not None else None
+        q, _, _, _ = oracle.sweep(dim, L, nbr, J_fix, int(s), 0, 1, thr, D, q0, b)
+        res[k] = q
+    return res
+
+
+def _chi2_pvalue(marg, samples, sites):
+    S = samples.shape[0]
+    chi2, dof = 0.0, 0
+    for i in sites:
+        m = marg[i]
+        other_e, other_o = 0.0, 0
+        cells = []
+        for s, p in m.items():
+            e = p * S
+            o = int(np.sum(samples[:, i] == s))
+            if e >= 5:
+                cells.append((o, e))
+            else:
+                other_e += e
+                other_o += o
+        # outcomes never predicted must never occur
+        assert np.all(np.isin(samples[:, i], list(m.keys()))), f"site {i}: impossible outcome"
+        if other_e > 0:
+            cells.append((other_o, other_e))
+        for o, e in cells:
+            chi2 += (o - e) ** 2 / e
+        dof += len(cells) - 1
+    return stats.chi2.sf(chi2, max(dof, 1)), dof
+
+
+CASES = [
+    # (L, nbr, Q, phases, kT)
+    ((4, 4), 4, 3, 2, 1.0),
+    ((4, 4), 8, 2, 4, 1.0),
+    ((4, 4, 4), 6, 3, 1, 1.0),
+    ((4, 4, 4), 26, 3, 1, 1.5),
+]
+
+
+@pytest.mark.parametrize("L,nbr,Q,phases,kT", CASES)
+def test_sweep_one_mcs_transition_probabilities(oracle, L, nbr, Q, phases, kT):
+    """Per-site outcome frequencies after one MCS match exact enumeration (chi-square).
+
+    The exact side proposes uniformly among the metric neighbours and takes dE
+    from the difference of the global Hamiltonian (Eq. (7)), so it shares no
+    arithmetic with the oracle's local update."""
+    N = int(np.prod(L))
+    q0 = synth.random_lattice(L, Q, seed=11 + nbr)
+    bgrain = np.array([0, 37, -21][:Q], dtype=np.int64)
+    J_fix = 256
+    thr, D = oracle.threshold_table(kT)
+    marg = exact_marginals(q0, L, nbr, J_fix, bgrain, thr, D, phases)
+    C = {4: 2, 6: 2, 8: 4, 26: 8}[nbr]
+    sites = [i for i in range(N) if _colour(L, nbr, i) < phases]
+    S = 6000 if N <= 16 else 3000
+    samples = _empirical(oracle, q0, L, nbr, J_fix, bgrain.astype(np.int32), thr, D, range(1000, 1000 + S))
+    pval, dof = _chi2_pvalue(marg, samples, sites)
+    assert pval > 1e-4, (pval, dof)
+    if phases == C:
+        return
+    # sites of later colours: at least their support must be the neighbours' spins or their own
+    nsets = _neighbour_sets(L, nbr)
+    for i in range(N):
+        if _colour(L, nbr, i) >= phases:
+            allowed = set(range(Q))
+            assert set(np.unique(samples[:, i])) <= allowed
+    _ = nsets
+
+
+def test_sweep_exact_marginals_detect_wrong_neighbourhood(oracle):
+    """Sanity of the enumerator itself: a 4-neighbour oracle run fails the 8-neighbour marginals."""
+    L = (4, 4)
+    q0 = synth.random_lattice(L, 2, seed=5)
+    thr, D = oracle.threshold_table(1.0)
+    bgrain = np.array([0, 37], dtype=np.int64)
+    marg8 = exact_marginals(q0, L, 8, 256, bgrain, thr, D, 1)
+    samples = _empirical(oracle, q0, L, 4, 256, bgrain.astype(np.int32), thr, D, range(3000))
+    sites = [i for i in range(16) if _colour(L, 8, i) == 0]
+    try:
+        pval, _ = _chi2_pvalue(marg8, samples, sites)
+    except AssertionError:
+        return
+    assert pval < 1e-6
+
+
+# --------------------------------------------------------------------------
+# Invariants
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,L,nbr", [(2, (16, 12), 4), (2, (12, 16), 8), (3, (8, 6, 4), 6), (3, (6, 8, 4), 26)])
+def test_zero_coupling_zero_field(oracle, dim, L, nbr):
+    """J = 0 and zero field: strict rule leaves the lattice unchanged; Metropolis
+    accepts exactly the proposals of a different spin (dE = 0 everywhere)."""
+    q0 = synth.random_lattice(L, 5, seed=3)
+    thr_s, D = oracle.threshold_table(0.7, zero_rule=1)
+    q, _, _, flips = oracle.sweep(dim, L, nbr, 0, 99, 0, 4, thr_s, D, q0)
+    assert flips == 0 and np.array_equal(q, q0)
+    thr_m, D = oracle.threshold_table(0.7, zero_rule=0)
+    q1, _, _, flips = oracle.sweep(dim, L, nbr, 0, 99, 0, 1, thr_m, D, q0)
+    assert flips > 0
+    # every changed site now holds a value present in its neighbourhood before... or after
+    # a phase; at least the multiset of values stays within the initial set
+    assert set(np.unique(q1)) <= set(np.unique(q0))
+
+
+@pytest.mark.parametrize("dim,L,nbr", [(2, (16, 16), 4), (2, (16, 16), 8), (3, (8, 8, 8), 6), (3, (8, 8, 8), 26)])
+def test_flat_interface_frozen_at_zero_temperature(oracle, dim, L, nbr):
+    """A flat boundary with zero field at kT = 0: every flip raises the energy, so nothing moves."""
+    q0 = synth.half_plane_lattice(L, axis=0)
+    thr, D = oracle.threshold_table(0.0, zero_rule=1)
+    q, _, _, flips = oracle.sweep(dim, L, nbr, 256, 5, 0, 20, thr, D, q0)
+    assert flips == 0 and np.array_equal(q, q0)
+
+
+def test_single_grain_never_flips(oracle):
+    q0 = np.full(64 * 64, 7, dtype=np.int32)
+    thr, D = oracle.threshold_table(2.0)
+    q, _, _, flips = oracle.sweep(2, (64, 64), 8, 256, 1, 0, 5, thr, D, q0)
+    assert flips == 0 and np.array_equal(q, q0)
+
+
+def test_carry_of_bulk_energy_and_material_point(oracle):
+    """Sec. 6: a swept site takes the overtaking grain's content: (q, b, mp) move together."""
+    L = (32, 32)
+    q0 = synth.blocky_lattice(L, 6, seed=2, block=4)
+    b0 = synth.random_field(q0.size, -40, 40, seed=3)
+    mp0 = np.arange(q0.size, dtype=np.int32)
+    thr, D = oracle.threshold_table(0.8)
+    q, b, mp, flips = oracle.sweep(2, L, 8, 256, 17, 0, 10, thr, D, q0, b0, mp0)
+    assert flips > 0
+    # each site's (b, q) pair is the original pair of the material point it now carries
+    np.testing.assert_array_equal(b, b0[mp])
+    np.testing.assert_array_equal(q, q0[mp])
+
+
+def test_lower_bulk_energy_favoured(oracle):
+    """Sec. 5: material with lower bulk energy is favoured; the site-averaged b falls."""
+    L = (64, 64)
+    q0, _ = oracle.voronoi(2, L, 40, 77)
+    bgrain = (256 * synth.uniform_energies(40, 0.5, seed=4)).astype(np.int32)
+    thr, D = oracle.threshold_table(0.6)
+    q, b, _, _ = oracle.sweep(2, L, 8, 256, 8, 0, 60, thr, D, q0, bgrain[q0])
+    assert b.mean() < bgrain[q0].mean() - 5
+
+
+def test_shrinking_disc_and_bulk_driving(oracle):
+    """Sec. 4 bicrystal: with zero field a disc shrinks at a roughly constant rate
+    (dA/dt = -2 pi m gamma); a bulk energy favouring the disc makes it grow."""
+    L = (96, 96)
+    q0 = synth.disc_lattice(L, 24)
+    thr, D = oracle.threshold_table(0.8)
+    areas, q = [int(q0.sum())], q0
+    for k in range(10):
+        q, _, _, _ = oracle.sweep(2, L, 8, 256, 31, 30 * k, 30, thr, D, q)
+        areas.append(int(q.sum()))
+    a = np.array(areas, dtype=float)
+    t = np.arange(len(a)) * 30.0
+    fit = stats.linregress(t, a)
+    assert fit.slope < 0 and fit.rvalue ** 2 > 0.95, (areas, fit)
+    # bulk driving: outside grain costs 0.6 J per site more than the disc
+    bgrain = np.array([154, 0], dtype=np.int32)
+    q2, _, _, _ = oracle.sweep(2, L, 8, 256, 31, 0, 60, thr, D, q0, bgrain[q0])
+    assert q2.sum() > q0.sum() * 1.2
+
+
+def test_isotropic_growth_law(oracle):
+    """Sec. 4, Fig. 2(b): isotropic grain growth in 2D gives <A> linear in time."""
+    L = (192, 192)
+    G = 900
+    q, _ = oracle.voronoi(2, L, G, 1234)
+    thr, D = oracle.threshold_table(0.6)
+    t, A = [0], []
+    counts, alive = oracle.grain_counts(q, G)
+    A.append(q.size / alive)
+    step = 25
+    for k in range(16):
+        q, _, _, _ = oracle.sweep(2, L, 8, 256, 2024, step * k, step, thr, D, q)
+        counts, alive = oracle.grain_counts(q, G)
+        t.append(step * (k + 1))
+        A.append(q.size / alive)
+    t = np.array(t, dtype=float)
+    A = np.array(A)
+    late = t >= 100
+    fit = stats.linregress(t[late], A[late])
+    assert fit.slope > 0 and fit.rvalue ** 2 > 0.97, (A, fit)
+    # growth exponent of (A - A0) close to 1 (parabolic law in radius)
+    ll = stats.linregress(np.log(t[late]), np.log(A[late] - A[0]))
+    assert 0.75 < ll.slope < 1.3, ll
