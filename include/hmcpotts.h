@@ -1,0 +1,209 @@
+/*
+ * hmcpotts.h -- C ABI of the GB300 (sm_103a) hybrid Monte Carlo grain-growth
+ * library: checkerboard Potts sweep driven by a stored-energy field from
+ * Monte Carlo crystal plasticity (Zhang, Dingreville, Bartel, Lusk,
+ * "Hybrid Monte Carlo Simulation of Stress-Induced Texture Evolution with
+ * Inelastic Effects", arXiv 1007.3509).
+ *
+ * Conventions
+ *  - Every call returns int: HP_OK (0) or a negative HP_ERR_* code.  A failed
+ *    call leaves a message readable with hp_last_error_message().
+ *  - Pointers documented "device" are CUDA device pointers; "host" pointers
+ *    are ordinary host memory.  Device buffers passed to hp_bind() and
+ *    hp_set_field() are BORROWED: the caller owns them and keeps them alive
+ *    until hp_destroy() or until they are re-bound.  Everything else the
+ *    library allocates itself and frees in hp_destroy().
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  GPU calls are asynchronous on that stream unless documented
+ *    otherwise.  A handle may be used from one host thread at a time.
+ *  - Lattices are periodic boxes with even edges, linear site index
+ *    x + Lx*(y + Ly*z), int32 grain ids q (the Potts spins of Eq. (7)).
+ *  - Energies inside the sweep are int32 fixed point: 256 units = 1 J, the
+ *    interaction energy unit of Eq. (7).
+ */
+#ifndef HMCPOTTS_H
+#define HMCPOTTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HP_API __attribute__((visibility("default")))
+#else
+#define HP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HP_OK 0
+#define HP_ERR_ARG (-1)      /* invalid argument or unsupported combination      */
+#define HP_ERR_CUDA (-2)     /* a CUDA runtime call or kernel launch failed      */
+#define HP_ERR_OOM (-3)      /* device allocation failed                         */
+#define HP_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up               */
+#define HP_ERR_STATE (-5)    /* call made in the wrong order (e.g. nothing bound) */
+#define HP_ERR_CHECKSUM (-6) /* checkpoint file corrupted                        */
+
+/* Field modes: where the per-site bulk energy b_i of Eq. (7) comes from.     */
+#define HP_FIELD_NONE 0   /* b = 0                                             */
+#define HP_FIELD_GRAIN 1  /* b_i = table[q_i]  (one energy per grain, G entries) */
+#define HP_FIELD_POINT 2  /* b_i = table[mp_i] (one energy per material point;   */
+                          /*  mp is carried with q when a boundary sweeps a site) */
+
+/* Orientation kinds. */
+#define HP_ORIENT_ANGLE 0 /* one rotation angle about z in [0, pi/2), float[G]  */
+#define HP_ORIENT_SO3 1   /* unit quaternion (w,x,y,z) uniform on SO(3), float[4G] */
+
+/* Sweep kernel choice (hp_set_sweep_kernel). */
+#define HP_SWEEP_AUTO 0   /* fused multi-phase tiles where available            */
+#define HP_SWEEP_PHASE 1  /* one launch per colour phase, in place              */
+#define HP_SWEEP_FUSED 2  /* all phases of a plane in shared memory, double-buffered */
+
+typedef struct {
+    int32_t dim;        /* 2 or 3                                             */
+    int64_t L[3];       /* edges; even; L[2] ignored (treated as 1) in 2D     */
+    int32_t nbr;        /* neighbours M: 4 or 8 in 2D, 6 or 26 in 3D          */
+    int32_t J_fix;      /* interaction energy J in fixed point (J = 1 -> 256) */
+    uint64_t seed;      /* Philox4x32-10 key of this lattice                  */
+    int32_t n_grains;   /* G: grain ids are 0..G-1                            */
+    int32_t field_mode; /* HP_FIELD_*                                         */
+} hp_desc;
+
+typedef struct hp_handle hp_handle;
+
+/* Latest error message of this thread (never NULL). */
+HP_API const char* hp_last_error_message(void);
+
+/* Library build/version string (never NULL). */
+HP_API const char* hp_version(void);
+
+/* Create a lattice handle.  Validates the descriptor (Sec. 4: square or cubic
+ * lattice, M neighbours; colour count follows from nbr: 2 for 4/6, 4 for 2D-8,
+ * 8 for 3D-26).  No device memory is touched.                                */
+HP_API int hp_create(const hp_desc* desc, hp_handle** out);
+
+/* Free everything the library allocated for the handle.  Safe with NULL.      */
+HP_API int hp_destroy(hp_handle* h);
+
+/* Bind the caller's device buffers: q (int32[N], required) and mp (int32[N],
+ * required in HP_FIELD_POINT mode, else may be NULL).  Allocates the library's
+ * double-buffer copies (same sizes) used by the fused sweep.                  */
+HP_API int hp_bind(hp_handle* h, int32_t* q, int32_t* mp);
+
+/* Initial polycrystal (Sec. 4-5 set-up): Voronoi tessellation of G seeds.
+ * Seeds are drawn in rounds from Philox(seed; g, round, tag 2 | 0); a site
+ * drawn by several seeds goes to the lowest g, losers redraw.  Every site gets
+ * the seed at the smallest periodic minimum-image squared integer distance,
+ * ties to the lowest index.  Writes q, sets mp to the identity when bound, and
+ * writes G orientations of `orient_kind` into orient (device float[G] or
+ * float[4G]; may be NULL) and the seed sites into seed_pos (device int64[G];
+ * may be NULL).  Synchronises `stream` once per seeding round.               */
+HP_API int hp_init_voronoi(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, void* stream);
+
+/* Orientations only (same draws as hp_init_voronoi).                          */
+HP_API int hp_orientations(int32_t G, uint64_t seed, int32_t orient_kind, float* orient, void* stream);
+
+/* Stored-energy field table (borrowed device int32): G entries in
+ * HP_FIELD_GRAIN mode, N entries (one per material point) in HP_FIELD_POINT. */
+HP_API int hp_set_field(hp_handle* h, const int32_t* table, int64_t n);
+
+/* Metropolis threshold table, host FP64 (Sec. 4, acceptance
+ * min(1, exp(-dE/kT))): out[0] = 0xFFFFFFFF (dE = 0 accepted) or 0 when
+ * zero_rule = 1; out[d] = min(floor(2^32 exp(-d/(256 kT))), 0xFFFFFFFE) for
+ * d >= 1 up to *D, the last nonzero entry (D = 0 when kT = 0).  `cap` is the
+ * capacity of out; HP_ERR_ARG if the table does not fit.                     */
+HP_API int hp_build_threshold_table(double kT, int32_t zero_rule, uint32_t* out, int32_t cap, int32_t* D);
+
+/* Copy a threshold table (host uint32[D+1]) to the device for this handle.   */
+HP_API int hp_set_threshold_table(hp_handle* h, const uint32_t* thr, int32_t D, void* stream);
+
+/* Choose the sweep kernel (HP_SWEEP_*); both give bit-identical lattices.    */
+HP_API int hp_set_sweep_kernel(hp_handle* h, int32_t kind);
+
+/* Run n_mcs Monte Carlo steps (Sec. 4): each step runs colours 0..C-1 in
+ * order; a colour phase updates all its sites from the state left by the
+ * previous phase.  Site i of colour c draws Philox(seed; i, sweep, tag 0 | c),
+ * proposes neighbour k = (u0*M)>>32, and with q_j != q_i computes
+ * d = J_fix*(#nbrs equal q_i - #nbrs equal q_j) + (b_j - b_i); accepts if
+ * d < 0, rejects if d > D, else accepts iff thr[d] = 0xFFFFFFFF or u1 < thr[d].
+ * An accepted site copies q_j and mp_j (Sec. 6: the swept site takes the
+ * content of the overtaking grain).  `sweep` starts at the handle's counter,
+ * which advances by n_mcs.  On return the state is in the bound buffers.     */
+HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
+
+HP_API int hp_get_sweep_counter(const hp_handle* h, uint64_t* out);
+HP_API int hp_set_sweep_counter(hp_handle* h, uint64_t value);
+
+/* Per-grain site counts (device int64[G]) and the number of grains with a
+ * nonzero count (device int32[1]) of the bound lattice (Sec. 4: average grain
+ * size N / alive).                                                           */
+HP_API int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, void* stream);
+
+/* Texture (Sec. 5): per-grain bins of the orientations and the area-weighted
+ * histogram hist[b] = sum of counts of grains in bin b (device int64).
+ * HP_ORIENT_ANGLE: 90 one-degree bins of the angle; bins int32[G].
+ * HP_ORIENT_SO3: 20 bins of the max Schmid factor over [0, 0.5] followed by
+ * 4 bins (none, <100>, <110>, <111> within 15 degrees of the loading axis x);
+ * bins int32[2G]; hist int64[24].                                            */
+HP_API int hp_texture(int32_t G, int32_t orient_kind, const float* orient, const int64_t* counts, int32_t* bins,
+               int64_t* hist, void* stream);
+
+/* Closed-form per-grain field under uniaxial stress sigma [MPa] along x
+ * (Sec. 5): d = loading axis in the crystal frame, E(d) the directional
+ * Young's modulus of cubic (C11, C12, C44) [MPa], w = sigma^2/(2 E(d)),
+ * m_max = largest FCC {111}<110> Schmid factor of d; the energy
+ * e = energy_scale * (w + k_disl * m_max) [J] is quantised to
+ * b = round-half-even(256 e) clamped to +-2^20.  quat: device float[4G];
+ * b_out device int32[G]; w_out, mmax_out device float[G] or NULL.           */
+HP_API int hp_grain_field(int32_t G, const float* quat, double C11, double C12, double C44, double sigma,
+                   double k_disl, double energy_scale, int32_t* b_out, float* w_out, float* mmax_out,
+                   void* stream);
+
+/* Philox4x32-10 of n counters (device uint32[4n]) into out (device uint32[4n]),
+ * the generator every kernel here draws from (exposed for verification).     */
+HP_API int hp_philox(uint64_t seed, const uint32_t* ctr, int64_t n, uint32_t* out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Monte Carlo crystal plasticity (Sec. 2, Eqs. (1)-(3), Table 1) and the     */
+/* per-point field of Eq. (4).                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double C11, C12, C44;    /* cubic moduli [MPa]                              */
+    double tau0, taus, h0;   /* Voce hardening: g = taus - (taus-tau0) exp(-h0 gamma/(taus-tau0)) */
+    double beta;             /* inverse temperature of Eq. (1) [per MJ/m^3]     */
+    double G;                /* shear modulus of Eq. (4) [MPa]                  */
+    double e_incr;           /* strain increment e of Eq. (3)                   */
+    double energy_scale;     /* J (MC units) per MJ/m^3 for the field           */
+} hp_cp_params;
+
+/* Material-point state, structure of arrays over P points (device memory):
+ * eps_p float[6][P] (components xx yy zz yz xz xy, crystal frame), gamma
+ * float[P] (accumulated slip), g float[P] (slip resistance).                 */
+typedef struct {
+    int64_t P;
+    float* eps_p;
+    float* gamma;
+    float* g;
+} hp_cp_state;
+
+/* Zero plastic strain and slip, g = tau0.                                    */
+HP_API int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream);
+
+/* Apply load increments t = t0+1 .. t0+n_incr to every point (Eq. (3), Taylor:
+ * total strain t e diag(1,-1/2,-1/2) in the sample frame).  Point p has the
+ * orientation quat[4*grain[p]].  Per increment: trial stress, candidate set
+ * |tau_alpha| > g, single-slip return map per candidate (FP64 Newton), energies
+ * E_alpha, Boltzmann probabilities (Eq. (1)) and the pick of Eq. (2) with
+ * R = u0/2^32 of Philox(seed; p, t, tag 1).  Afterwards, optionally writes
+ * sigma (device float[6][P], NULL to skip), w and E_rho (device float[P] each,
+ * NULL to skip; E_rho = 2 g^2/G, w = 1/2 sigma : C^-1 : sigma) and the
+ * quantised field b = round-half-even(256 energy_scale (w + E_rho)) (device
+ * int32[P], NULL to skip) for HP_FIELD_POINT.                                */
+HP_API int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat, uint32_t t0,
+               int32_t n_incr, hp_cp_state* st, float* sigma, float* w, float* erho, int32_t* b, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMCPOTTS_H */

@@ -1,0 +1,93 @@
+// Internal definitions shared by the library's translation units.
+// (Device side: Philox, lattice geometry; host side: error plumbing and the
+// handle layout.)  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hmcpotts.h"
+
+namespace hp {
+
+// ---------------------------------------------------------------------------
+// Errors: thread-local last message, HP_* codes.
+// ---------------------------------------------------------------------------
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+#define HP_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) return ::hp::cuda_error(_e, #call); \
+    } while (0)
+
+#define HP_LAUNCH_CHECK(what)                                     \
+    do {                                                          \
+        cudaError_t _e = cudaGetLastError();                      \
+        if (_e != cudaSuccess) return ::hp::cuda_error(_e, what); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).  Counter words: unit lo, unit hi,
+// step, tag << 24 | sub.  Key: seed lo, seed hi.
+// ---------------------------------------------------------------------------
+enum : uint32_t { kTagSweep = 0, kTagMcp = 1, kTagVoronoi = 2, kTagSurrogate = 3 };
+
+__device__ __forceinline__ uint4 philox10(uint32_t k0, uint32_t k1, uint4 c) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint64_t unit, uint32_t step, uint32_t tag, uint32_t sub) {
+    return philox10((uint32_t)seed, (uint32_t)(seed >> 32),
+                     make_uint4((uint32_t)unit, (uint32_t)(unit >> 32), step, (tag << 24) | sub));
+}
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct Lattice {
+    int dim;
+    int64_t L[3];  // L[2] = 1 in 2D
+    int nbr;
+    int colours;
+    int64_t N;
+};
+
+}  // namespace hp
+
+struct hp_handle {
+    hp_desc desc;
+    hp::Lattice lat;
+    int32_t* q = nullptr;       // borrowed
+    int32_t* mp = nullptr;      // borrowed (may be null)
+    int32_t* q_alt = nullptr;   // owned double buffers
+    int32_t* mp_alt = nullptr;
+    const int32_t* table = nullptr;  // borrowed field table
+    int64_t table_n = 0;
+    uint32_t* thr = nullptr;    // owned device threshold table
+    int32_t D = -1;
+    int32_t thr_cap = 0;
+    uint64_t sweep = 0;
+    int sweep_kernel = HP_SWEEP_AUTO;
+};
+
+namespace hp {
+// launchers (sweep.cu)
+int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s);
+// launchers (voronoi.cu)
+int voronoi_run(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, cudaStream_t s);
+int orientations_run(int32_t G, uint64_t seed, int32_t kind, float* orient, cudaStream_t s);
+}  // namespace hp

@@ -1,0 +1,289 @@
+// Monte Carlo crystal plasticity (Sec. 2, Eqs. (1)-(3), Table 1) and the
+// per-point driving field (Sec. 3, Eq. (4)).  One thread per material point.
+//
+// Per increment t (Eq. (3), Taylor: every point takes the prescribed strain):
+//   eps_c = R^T (t e diag(1,-1/2,-1/2)) R          crystal-frame total strain
+//   ee = eps_c - eps_p; s = C : ee                   trial stress (FP32)
+//   tau_a = m_a . s . n_a; zeta = {a : |tau_a| > g}  candidates (FP32)
+//   per candidate, the single-slip return map |tau_a| - x k = g(gamma + x),
+//   k = P:C:P, Voce g(gamma + x) = taus - (taus - g) exp(-h0 x/(taus - tau0)),
+//   solved by Newton in FP64;
+//   energy change of the candidate state  dE_a = -x |tau_a| + x^2 k / 2
+//   (E_a = 1/2 ee_a : C : ee_a with ee_a = ee - x sign(tau_a) P_a);
+//   p_a = exp(-beta (dE_a - min dE)) / Z (Eq. (1)); R = u0 / 2^32 from
+//   Philox(seed; p, t, tag 1); first a with R < sum_{b<=a} p_b (Eq. (2));
+//   commit eps_p += x sign P, gamma += x, g = g(gamma + x).
+// After the last increment: sigma = C : (eps_c - eps_p); E_rho = 2 g^2 / G
+// (Eq. (4) with sigma_f = g; the Burgers vector cancels); w = 1/2 sigma : ee;
+// b = round-half-even(256 scale (w + E_rho)) clamped to +-2^20.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hp {
+namespace {
+
+constexpr int kT = 128;
+
+__constant__ float c_m[12][3];
+__constant__ float c_n[12][3];
+__constant__ double c_k[12];  // P:C:P per system
+
+struct CPArgs {
+    float C11, C12, C44;
+    double tau0, taus, h0;
+    float beta;
+    float G;
+    float e;
+    float scale;
+    uint64_t seed;
+    const int32_t* grain;
+    const float* quat;
+    uint32_t t0;
+    int32_t n_incr;
+    int64_t P;
+    float* eps_p;
+    float* gamma;
+    float* g;
+    float* sigma;
+    float* w;
+    float* erho;
+    int32_t* b;
+};
+
+__device__ __forceinline__ void stress(const CPArgs& a, const float ee[6], float s[6]) {
+    const float tr = ee[0] + ee[1] + ee[2];
+    const float d = a.C11 - a.C12;
+    s[0] = d * ee[0] + a.C12 * tr;
+    s[1] = d * ee[1] + a.C12 * tr;
+    s[2] = d * ee[2] + a.C12 * tr;
+    s[3] = 2.0f * a.C44 * ee[3];
+    s[4] = 2.0f * a.C44 * ee[4];
+    s[5] = 2.0f * a.C44 * ee[5];
+}
+
+// exp(-y) for y >= 0: Taylor series for small y, libm otherwise.
+__device__ __forceinline__ double exp_neg(double y) {
+    if (y < 0.02) {
+        // truncation after y^6/720: below 1e-16 relative for y < 0.02
+        return 1.0 - y * (1.0 - y * (0.5 - y * (1.0 / 6.0 - y * (1.0 / 24.0 - y * (1.0 / 120.0 - y * (1.0 / 720.0))))));
+    }
+    return exp(-y);
+}
+
+__global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.P) return;
+    const float* qq = a.quat + 4 * (int64_t)a.grain[p];
+    float qw = qq[0], qx = qq[1], qy = qq[2], qz = qq[3];
+    const float inv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= inv; qx *= inv; qy *= inv; qz *= inv;
+    float R[3][3];
+    R[0][0] = 1.f - 2.f * (qy * qy + qz * qz); R[0][1] = 2.f * (qx * qy - qw * qz); R[0][2] = 2.f * (qx * qz + qw * qy);
+    R[1][0] = 2.f * (qx * qy + qw * qz); R[1][1] = 1.f - 2.f * (qx * qx + qz * qz); R[1][2] = 2.f * (qy * qz - qw * qx);
+    R[2][0] = 2.f * (qx * qz - qw * qy); R[2][1] = 2.f * (qy * qz + qw * qx); R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+    // unit-strain crystal-frame tensor U = R^T diag(1,-1/2,-1/2) R (Voigt order xx yy zz yz xz xy)
+    const int I[6] = {0, 1, 2, 1, 0, 0}, J[6] = {0, 1, 2, 2, 2, 1};
+    float U[6];
+#pragma unroll
+    for (int v = 0; v < 6; ++v)
+        U[v] = R[0][I[v]] * R[0][J[v]] - 0.5f * (R[1][I[v]] * R[1][J[v]] + R[2][I[v]] * R[2][J[v]]);
+    float ep[6];
+#pragma unroll
+    for (int v = 0; v < 6; ++v) ep[v] = a.eps_p[(int64_t)v * a.P + p];
+    float gam = a.gamma[p];
+    float gres = a.g[p];
+    const double dtau = a.taus - a.tau0;
+    const bool hard = dtau > 0.0 && a.h0 > 0.0;
+    const double hr = hard ? a.h0 / dtau : 0.0;
+    float ee[6], s[6];
+    for (int32_t inc = 1; inc <= a.n_incr; ++inc) {
+        const uint32_t t = a.t0 + (uint32_t)inc;
+        const float et = (float)t * a.e;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) ee[v] = et * U[v] - ep[v];
+        stress(a, ee, s);
+        float tau[12];
+        int mask = 0;
+#pragma unroll
+        for (int al = 0; al < 12; ++al) {
+            const float m0 = c_m[al][0], m1 = c_m[al][1], m2 = c_m[al][2];
+            const float n0 = c_n[al][0], n1 = c_n[al][1], n2 = c_n[al][2];
+            // m . s . n with s symmetric: s = [[s0,s5,s4],[s5,s1,s3],[s4,s3,s2]]
+            tau[al] = m0 * (s[0] * n0 + s[5] * n1 + s[4] * n2) + m1 * (s[5] * n0 + s[1] * n1 + s[3] * n2) +
+                      m2 * (s[4] * n0 + s[3] * n1 + s[2] * n2);
+            if (fabsf(tau[al]) > gres) mask |= 1 << al;
+        }
+        if (!mask) continue;
+        double x[12], dE[12];
+        double dEmin = 1e300;
+        const double g0 = gres;
+#pragma unroll
+        for (int al = 0; al < 12; ++al) {
+            if (!(mask >> al & 1)) continue;
+            const double at = fabs((double)tau[al]);
+            const double k = c_k[al];
+            double xx;
+            if (!hard) {
+                xx = (at - g0) / k;
+            } else {
+                const double sat = a.taus - g0;  // taus - g
+                xx = (at - g0) / (k + sat * hr);
+#pragma unroll 1
+                for (int it = 0; it < 8; ++it) {
+                    const double ey = exp_neg(hr * xx);
+                    const double f = at - xx * k - (a.taus - sat * ey);
+                    const double fp = -k - sat * hr * ey;
+                    const double dx = f / fp;
+                    xx -= dx;
+                    if (fabs(f) < 1e-13 * a.tau0) break;
+                }
+            }
+            x[al] = xx;
+            dE[al] = -xx * at + 0.5 * xx * xx * k;
+            dEmin = fmin(dEmin, dE[al]);
+        }
+        float wgt[12];
+        double Z = 0.0;
+#pragma unroll
+        for (int al = 0; al < 12; ++al) {
+            wgt[al] = (mask >> al & 1) ? expf(-a.beta * (float)(dE[al] - dEmin)) : 0.0f;
+            Z += (double)wgt[al];
+        }
+        const uint4 u = draw(a.seed, (uint64_t)p, t, kTagMcp, 0);
+        const double Rn = (double)u.x * (1.0 / 4294967296.0);
+        double cum = 0.0;
+        int pick = -1, last = -1;
+#pragma unroll
+        for (int al = 0; al < 12; ++al) {
+            if (!(mask >> al & 1)) continue;
+            last = al;
+            cum += (double)wgt[al] / Z;
+            if (pick < 0 && Rn < cum) pick = al;
+        }
+        if (pick < 0) pick = last;
+        const double xs = x[pick];
+        const float sg = tau[pick] > 0.f ? 1.f : -1.f;
+        const float m0 = c_m[pick][0], m1 = c_m[pick][1], m2 = c_m[pick][2];
+        const float n0 = c_n[pick][0], n1 = c_n[pick][1], n2 = c_n[pick][2];
+        const float xf = (float)xs * sg;
+        ep[0] += xf * m0 * n0;
+        ep[1] += xf * m1 * n1;
+        ep[2] += xf * m2 * n2;
+        ep[3] += xf * 0.5f * (m1 * n2 + m2 * n1);
+        ep[4] += xf * 0.5f * (m0 * n2 + m2 * n0);
+        ep[5] += xf * 0.5f * (m0 * n1 + m1 * n0);
+        gam += (float)xs;
+        gres = hard ? (float)(a.taus - (a.taus - g0) * exp_neg(hr * xs)) : gres;
+    }
+#pragma unroll
+    for (int v = 0; v < 6; ++v) a.eps_p[(int64_t)v * a.P + p] = ep[v];
+    a.gamma[p] = gam;
+    a.g[p] = gres;
+    if (a.sigma || a.w || a.erho || a.b) {
+        const uint32_t t = a.t0 + (uint32_t)a.n_incr;
+        const float et = (float)t * a.e;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) ee[v] = et * U[v] - ep[v];
+        stress(a, ee, s);
+        if (a.sigma)
+#pragma unroll
+            for (int v = 0; v < 6; ++v) a.sigma[(int64_t)v * a.P + p] = s[v];
+        const float w = 0.5f * (s[0] * ee[0] + s[1] * ee[1] + s[2] * ee[2]) + (s[3] * ee[3] + s[4] * ee[4] + s[5] * ee[5]);
+        const float er = 2.0f * gres * gres / a.G;
+        if (a.w) a.w[p] = w;
+        if (a.erho) a.erho[p] = er;
+        if (a.b) {
+            float v = rintf(256.0f * a.scale * (w + er));
+            v = fminf(fmaxf(v, -1048576.0f), 1048576.0f);
+            a.b[p] = (int32_t)v;
+        }
+    }
+}
+
+__global__ void k_cp_reset(int64_t P, float* eps_p, float* gamma, float* g, float tau0) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) eps_p[(int64_t)v * P + p] = 0.0f;
+    gamma[p] = 0.0f;
+    g[p] = tau0;
+}
+
+// Constant tables depend on the moduli only; re-upload when they change.
+double g_loaded[3] = {0.0, 0.0, 0.0};
+int g_loaded_dev = -1;
+
+int upload_tables(const hp_cp_params* prm) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    if (dev == g_loaded_dev && g_loaded[0] == prm->C11 && g_loaded[1] == prm->C12 && g_loaded[2] == prm->C44)
+        return HP_OK;
+    static const int N[12][3] = {{1, 1, 1},  {1, 1, 1},  {1, 1, 1},  {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
+                                 {1, -1, 1}, {1, -1, 1}, {1, -1, 1}, {1, 1, -1}, {1, 1, -1}, {1, 1, -1}};
+    static const int Mv[12][3] = {{0, 1, -1}, {-1, 0, 1}, {1, -1, 0}, {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
+                                  {0, 1, 1},  {1, 0, -1}, {1, 1, 0},  {0, 1, 1},  {1, 0, 1}, {1, -1, 0}};
+    float m[12][3], n[12][3];
+    double k[12];
+    const double sn = 1.0 / sqrt(3.0), sm = 1.0 / sqrt(2.0);
+    for (int a = 0; a < 12; ++a) {
+        double md[3], nd[3], P[3][3];
+        for (int i = 0; i < 3; ++i) {
+            md[i] = Mv[a][i] * sm;
+            nd[i] = N[a][i] * sn;
+            m[a][i] = (float)md[i];
+            n[a][i] = (float)nd[i];
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) P[i][j] = 0.5 * (md[i] * nd[j] + nd[i] * md[j]);
+        // P : C : P for cubic C
+        const double tr = P[0][0] + P[1][1] + P[2][2];
+        double v = 0.0;
+        for (int i = 0; i < 3; ++i) v += P[i][i] * ((prm->C11 - prm->C12) * P[i][i] + prm->C12 * tr);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (i != j) v += P[i][j] * 2.0 * prm->C44 * P[i][j];
+        k[a] = v;
+    }
+    HP_CUDA(cudaMemcpyToSymbol(c_m, m, sizeof m));
+    HP_CUDA(cudaMemcpyToSymbol(c_n, n, sizeof n));
+    HP_CUDA(cudaMemcpyToSymbol(c_k, k, sizeof k));
+    g_loaded[0] = prm->C11; g_loaded[1] = prm->C12; g_loaded[2] = prm->C44;
+    g_loaded_dev = dev;
+    return HP_OK;
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream) {
+    if (!prm || !st || st->P < 1 || !st->eps_p || !st->gamma || !st->g)
+        return set_error(HP_ERR_ARG, "hp_cp_reset: bad arguments");
+    k_cp_reset<<<(unsigned)((st->P + 255) / 256), 256, 0, as_stream(stream)>>>(st->P, st->eps_p, st->gamma, st->g,
+                                                                               (float)prm->tau0);
+    HP_LAUNCH_CHECK("k_cp_reset");
+    return HP_OK;
+}
+
+extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat,
+                          uint32_t t0, int32_t n_incr, hp_cp_state* st, float* sigma, float* w, float* erho,
+                          int32_t* b, void* stream) {
+    if (!prm || !st || !grain || !quat || n_incr < 0 || st->P < 1 || !st->eps_p || !st->gamma || !st->g)
+        return set_error(HP_ERR_ARG, "hp_cp_step: bad arguments");
+    if (!(prm->C11 > prm->C12) || !(prm->C44 > 0) || !(prm->tau0 > 0) || !(prm->G > 0))
+        return set_error(HP_ERR_ARG, "hp_cp_step: bad material constants");
+    int rc = upload_tables(prm);
+    if (rc) return rc;
+    CPArgs a;
+    a.C11 = (float)prm->C11; a.C12 = (float)prm->C12; a.C44 = (float)prm->C44;
+    a.tau0 = prm->tau0; a.taus = prm->taus; a.h0 = prm->h0;
+    a.beta = (float)prm->beta; a.G = (float)prm->G; a.e = (float)prm->e_incr; a.scale = (float)prm->energy_scale;
+    a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t0; a.n_incr = n_incr; a.P = st->P;
+    a.eps_p = st->eps_p; a.gamma = st->gamma; a.g = st->g;
+    a.sigma = sigma; a.w = w; a.erho = erho; a.b = b;
+    k_cp<<<(unsigned)((st->P + kT - 1) / kT), kT, 0, as_stream(stream)>>>(a);
+    HP_LAUNCH_CHECK("k_cp");
+    return HP_OK;
+}

@@ -1,0 +1,223 @@
+// Per-grain driving field in closed form, grain statistics and texture.
+//
+// Field (Sec. 5, uniaxial load along sample x): loading axis in the crystal
+// frame d = R(q)^T e_x; directional modulus of a cubic crystal
+//   1/E(d) = S11 - 2 (S11 - S12 - S44/2)(d1^2 d2^2 + d2^2 d3^2 + d3^2 d1^2),
+//   S11 = (C11+C12)/((C11-C12)(C11+2C12)), S12 = -C12/((C11-C12)(C11+2C12)),
+//   S44 = 1/C44;
+// elastic energy density w = sigma^2/(2E); max FCC {111}<110> Schmid factor
+// m_max = max_a |(d.n_a)(d.m_a)|; e = scale (w + k m_max) [J];
+// b = round-half-even(256 e), clamped to +-2^20.  One thread per grain, FP64.
+//
+// Statistics (Sec. 4 average grain size, Sec. 5 texture): per-grain site
+// counts, number of grains alive, per-grain texture bins and the
+// area-weighted histogram.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hp {
+namespace {
+
+constexpr int kT = 256;
+
+// FCC slip systems: plane normals and slip directions (unnormalised).
+__constant__ int8_t c_fcc_n[12][3] = {{1, 1, 1},  {1, 1, 1},  {1, 1, 1},  {-1, 1, 1}, {-1, 1, 1}, {-1, 1, 1},
+                                      {1, -1, 1}, {1, -1, 1}, {1, -1, 1}, {1, 1, -1}, {1, 1, -1}, {1, 1, -1}};
+__constant__ int8_t c_fcc_m[12][3] = {{0, 1, -1}, {-1, 0, 1}, {1, -1, 0}, {0, 1, -1}, {1, 0, 1}, {1, 1, 0},
+                                      {0, 1, 1},  {1, 0, -1}, {1, 1, 0},  {0, 1, 1},  {1, 0, 1}, {1, -1, 0}};
+
+__device__ void axis_from_quat(const float* qf, double d[3]) {
+    const double w0 = qf[0], x0 = qf[1], y0 = qf[2], z0 = qf[3];
+    const double n = sqrt(w0 * w0 + x0 * x0 + y0 * y0 + z0 * z0);
+    const double w = w0 / n, x = x0 / n, y = y0 / n, z = z0 / n;
+    // first row of the crystal-to-sample rotation matrix
+    d[0] = 1.0 - 2.0 * (y * y + z * z);
+    d[1] = 2.0 * (x * y - w * z);
+    d[2] = 2.0 * (x * z + w * y);
+}
+
+__device__ double max_schmid(const double d_in[3]) {
+    const double nn = sqrt(d_in[0] * d_in[0] + d_in[1] * d_in[1] + d_in[2] * d_in[2]);
+    const double d0 = d_in[0] / nn, d1 = d_in[1] / nn, d2 = d_in[2] / nn;
+    const double sn = 1.0 / sqrt(3.0), sm = 1.0 / sqrt(2.0);
+    double best = 0.0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        const double dn = (d0 * c_fcc_n[a][0] + d1 * c_fcc_n[a][1] + d2 * c_fcc_n[a][2]) * sn;
+        const double dm = (d0 * c_fcc_m[a][0] + d1 * c_fcc_m[a][1] + d2 * c_fcc_m[a][2]) * sm;
+        best = fmax(best, fabs(dn * dm));
+    }
+    return best;
+}
+
+struct FieldArgs {
+    const float* quat;
+    int32_t G;
+    double S11, S12, S44, sigma, k, scale;
+    int32_t* b;
+    float* w;
+    float* mmax;
+};
+
+__global__ void k_grain_field(FieldArgs a) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.G) return;
+    double d[3];
+    axis_from_quat(a.quat + 4 * g, d);
+    const double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double l = d[0] / nn, m = d[1] / nn, n = d[2] / nn;
+    const double inv_e = a.S11 - 2.0 * (a.S11 - a.S12 - 0.5 * a.S44) * (l * l * m * m + m * m * n * n + n * n * l * l);
+    const double w = 0.5 * a.sigma * a.sigma * inv_e;
+    const double mm = max_schmid(d);
+    const double e = a.scale * (w + a.k * mm);
+    double v = rint(256.0 * e);
+    v = fmin(fmax(v, -1048576.0), 1048576.0);
+    a.b[g] = (int32_t)v;
+    if (a.w) a.w[g] = (float)w;
+    if (a.mmax) a.mmax[g] = (float)mm;
+}
+
+// Per-grain counts: each thread scans a run of consecutive sites and adds the
+// length of each run of equal ids with one atomic.
+constexpr int kSeg = 32;
+
+__global__ void __launch_bounds__(kT) k_counts(const int32_t* __restrict__ q, int64_t N, int32_t G,
+                                               unsigned long long* counts, int32_t* bad) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = t * kSeg;
+    if (b >= N) return;
+    const int64_t e = b + kSeg < N ? b + kSeg : N;
+    int32_t cur = q[b];
+    unsigned long long run = 0;
+    for (int64_t i = b; i < e; ++i) {
+        const int32_t v = q[i];
+        if (v != cur) {
+            if ((uint32_t)cur < (uint32_t)G) atomicAdd(counts + cur, run); else atomicAdd(bad, 1);
+            cur = v;
+            run = 0;
+        }
+        ++run;
+    }
+    if ((uint32_t)cur < (uint32_t)G) atomicAdd(counts + cur, run); else atomicAdd(bad, 1);
+}
+
+__global__ void k_alive(const unsigned long long* counts, int32_t G, int32_t* alive) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = g < G && counts[g] > 0;
+    const int s = __syncthreads_count(v);
+    if (threadIdx.x == 0 && s) atomicAdd(alive, s);
+}
+
+__global__ void k_bins(int32_t G, int32_t kind, const float* orient, int32_t* bins) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const double pi = 3.14159265358979323846;
+    if (kind == HP_ORIENT_ANGLE) {
+        const double deg = (double)orient[g] * (180.0 / pi);
+        int b = (int)floor(deg);
+        bins[g] = b < 0 ? 0 : (b > 89 ? 89 : b);
+        return;
+    }
+    double d[3];
+    axis_from_quat(orient + 4 * g, d);
+    const double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double a0 = fabs(d[0] / nn), a1 = fabs(d[1] / nn), a2 = fabs(d[2] / nn);
+    const double ad[3] = {a0, a1, a2};
+    const double v = max_schmid(ad) / 0.5 * 20.0;
+    int b = (int)floor(v);
+    bins[2 * g] = b < 0 ? 0 : (b > 19 ? 19 : b);
+    const double c15 = cos(15.0 * pi / 180.0);
+    const double c100 = fmax(a0, fmax(a1, a2));
+    const double c110 = fmax(a0 + a1, fmax(a1 + a2, a0 + a2)) / sqrt(2.0);
+    const double c111 = (a0 + a1 + a2) / sqrt(3.0);
+    int fam = 0;
+    if (c100 > c15) fam = 1;
+    else if (c110 > c15) fam = 2;
+    else if (c111 > c15) fam = 3;
+    bins[2 * g + 1] = 20 + fam;
+}
+
+__global__ void k_hist(int32_t G, int32_t kind, const int32_t* bins, const unsigned long long* counts,
+                       unsigned long long* hist) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const unsigned long long c = counts[g];
+    if (!c) return;
+    if (kind == HP_ORIENT_ANGLE) {
+        atomicAdd(hist + bins[g], c);
+    } else {
+        atomicAdd(hist + bins[2 * g], c);
+        atomicAdd(hist + bins[2 * g + 1], c);
+    }
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" int hp_grain_field(int32_t G, const float* quat, double C11, double C12, double C44, double sigma,
+                              double k_disl, double energy_scale, int32_t* b_out, float* w_out, float* mmax_out,
+                              void* stream) {
+    if (G < 1 || !quat || !b_out) return set_error(HP_ERR_ARG, "hp_grain_field: bad arguments");
+    const double den = (C11 - C12) * (C11 + 2.0 * C12);
+    if (!(den != 0.0) || !(C44 != 0.0)) return set_error(HP_ERR_ARG, "hp_grain_field: singular moduli");
+    FieldArgs a;
+    a.quat = quat;
+    a.G = G;
+    a.S11 = (C11 + C12) / den;
+    a.S12 = -C12 / den;
+    a.S44 = 1.0 / C44;
+    a.sigma = sigma;
+    a.k = k_disl;
+    a.scale = energy_scale;
+    a.b = b_out;
+    a.w = w_out;
+    a.mmax = mmax_out;
+    k_grain_field<<<(G + kT - 1) / kT, kT, 0, as_stream(stream)>>>(a);
+    HP_LAUNCH_CHECK("k_grain_field");
+    return HP_OK;
+}
+
+extern "C" int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, void* stream) {
+    if (!h || !counts) return set_error(HP_ERR_ARG, "hp_grain_counts: bad arguments");
+    if (!h->q) return set_error(HP_ERR_STATE, "hp_grain_counts: no lattice bound");
+    cudaStream_t s = as_stream(stream);
+    const int32_t G = h->desc.n_grains;
+    HP_CUDA(cudaMemsetAsync(counts, 0, sizeof(int64_t) * G, s));
+    int32_t* bad = nullptr;
+    HP_CUDA(cudaMallocAsync((void**)&bad, sizeof(int32_t), s));
+    cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
+    const int64_t threads = (h->lat.N + kSeg - 1) / kSeg;
+    k_counts<<<(unsigned)((threads + kT - 1) / kT), kT, 0, s>>>(h->q, h->lat.N, G,
+                                                                reinterpret_cast<unsigned long long*>(counts), bad);
+    if (alive) {
+        cudaMemsetAsync(alive, 0, sizeof(int32_t), s);
+        k_alive<<<(G + kT - 1) / kT, kT, 0, s>>>(reinterpret_cast<const unsigned long long*>(counts), G, alive);
+    }
+    int32_t nbad = 0;
+    cudaMemcpyAsync(&nbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(bad, s);
+    HP_CUDA(cudaStreamSynchronize(s));
+    HP_LAUNCH_CHECK("k_counts");
+    if (nbad) return set_error(HP_ERR_STATE, "hp_grain_counts: lattice holds ids outside 0..G-1");
+    return HP_OK;
+}
+
+extern "C" int hp_texture(int32_t G, int32_t orient_kind, const float* orient, const int64_t* counts, int32_t* bins,
+                          int64_t* hist, void* stream) {
+    if (G < 1 || !orient || !bins || (orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_SO3))
+        return set_error(HP_ERR_ARG, "hp_texture: bad arguments");
+    cudaStream_t s = as_stream(stream);
+    k_bins<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, orient, bins);
+    if (hist && counts) {
+        const int nb = orient_kind == HP_ORIENT_ANGLE ? 90 : 24;
+        HP_CUDA(cudaMemsetAsync(hist, 0, sizeof(int64_t) * nb, s));
+        k_hist<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, bins,
+                                                 reinterpret_cast<const unsigned long long*>(counts),
+                                                 reinterpret_cast<unsigned long long*>(hist));
+    }
+    HP_LAUNCH_CHECK("k_bins/k_hist");
+    return HP_OK;
+}

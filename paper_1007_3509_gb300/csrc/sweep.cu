@@ -1,0 +1,500 @@
+// Checkerboard Potts sweep (Eq. (7), Sec. 4; bulk-energy carry, Sec. 6).
+//
+// Two kernels give bit-identical lattices:
+//  * k_phase  -- one launch per colour phase, one thread per site of that
+//    colour, neighbours read from global memory, state updated in place
+//    (no two sites of a colour are neighbours, so this equals the synchronous
+//    half-step of Sec. 4).
+//  * k_plane  -- all colour phases that live in one lattice plane are run on a
+//    shared-memory window of the plane (tile + halo of one site per phase),
+//    reading the previous state and writing the tile's new state to a second
+//    buffer.  2D lattices: one launch per MCS.  3D 26-neighbour lattices
+//    (colours 0-3 on even z planes, 4-7 on odd z planes): two launches per
+//    MCS, even planes first (their z neighbours are the old odd planes), then
+//    odd planes (z neighbours are the new even planes).
+//
+// Per site of colour c (sweep = MCS index):
+//   u = Philox(seed; site, sweep, tag 0 | c); k = (u.x * M) >> 32; j = nbr_k(i)
+//   if q_j == q_i: no change
+//   d = J*(#nbrs == q_i - #nbrs == q_j) + (b_j - b_i)
+//   accept: d < 0, or d <= D and (thr[d] == ~0 or u.y < thr[d])
+//   on accept q_i <- q_j, mp_i <- mp_j.
+// A site whose M neighbours all carry q_i cannot change; it skips the draw.
+#include "common.cuh"
+
+namespace hp {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int DIM, int NBR>
+struct Geo;
+
+// 2D-4: +x, -x, +y, -y ; colours (x+y)&1
+template <>
+struct Geo<2, 4> {
+    static constexpr int M = 4, C = 2;
+    __device__ static void off(int k, int& dx, int& dy, int& dz) {
+        dx = k == 0 ? 1 : (k == 1 ? -1 : 0);
+        dy = k == 2 ? 1 : (k == 3 ? -1 : 0);
+        dz = 0;
+    }
+};
+// 2D-8: (dy,dx) row-major without (0,0) ; colours (x&1) + 2(y&1)
+template <>
+struct Geo<2, 8> {
+    static constexpr int M = 8, C = 4;
+    __device__ static void off(int k, int& dx, int& dy, int& dz) {
+        const int kk = k + (k >= 4);
+        dy = kk / 3 - 1;
+        dx = kk % 3 - 1;
+        dz = 0;
+    }
+};
+// 3D-6: +x, -x, +y, -y, +z, -z ; colours (x+y+z)&1
+template <>
+struct Geo<3, 6> {
+    static constexpr int M = 6, C = 2;
+    __device__ static void off(int k, int& dx, int& dy, int& dz) {
+        dx = k == 0 ? 1 : (k == 1 ? -1 : 0);
+        dy = k == 2 ? 1 : (k == 3 ? -1 : 0);
+        dz = k == 4 ? 1 : (k == 5 ? -1 : 0);
+    }
+};
+// 3D-26: (dz,dy,dx) lexicographic without (0,0,0) ; colours (x&1)+2(y&1)+4(z&1)
+template <>
+struct Geo<3, 26> {
+    static constexpr int M = 26, C = 8;
+    __device__ static void off(int k, int& dx, int& dy, int& dz) {
+        const int kk = k + (k >= 13);
+        dz = kk / 9 - 1;
+        dy = (kk / 3) % 3 - 1;
+        dx = kk % 3 - 1;
+    }
+};
+
+__device__ __forceinline__ int wrapi(int a, int L) {
+    a %= L;
+    return a < 0 ? a + L : a;
+}
+
+__device__ __forceinline__ bool metropolis(int32_t d, int32_t D, const uint32_t* __restrict__ thr, uint32_t u) {
+    if (d < 0) return true;
+    if (d > D) return false;
+    const uint32_t t = __ldg(thr + d);
+    return t == 0xFFFFFFFFu || u < t;
+}
+
+// Field-table lookup with the index clamped into the table (ids come from
+// caller buffers; an out-of-range id must not read outside the table).
+__device__ __forceinline__ int32_t tab(const int32_t* __restrict__ t, uint32_t n, int32_t i) {
+    const uint32_t u = (uint32_t)i;
+    return __ldg(t + (u < n ? u : n - 1));
+}
+
+struct PhaseArgs {
+    int32_t* q;
+    int32_t* mp;
+    const int32_t* table;
+    uint32_t table_n;
+    const uint32_t* thr;
+    int32_t D, J;
+    uint64_t seed;
+    uint32_t sweep;
+    int colour;
+    int Lx, Ly, Lz;
+    int64_t n_colour_sites;
+};
+
+// ---------------------------------------------------------------------------
+// One colour phase, one thread per site of that colour, in place.
+// FIELD: 0 none, 1 grain (table[q]), 2 point (table[mp]).
+// ---------------------------------------------------------------------------
+template <int DIM, int NBR, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(kThreads) k_phase(PhaseArgs a) {
+    using G = Geo<DIM, NBR>;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_colour_sites) return;
+    const int c = a.colour;
+    const int hx = a.Lx >> 1;
+    int x, y, z;
+    if (G::C == 2) {
+        const int64_t r = t / hx;
+        const int k = (int)(t - r * hx);
+        y = (int)(r % a.Ly);
+        z = (int)(r / a.Ly);
+        x = 2 * k + ((y + z + c) & 1);
+    } else if (G::C == 4) {
+        const int64_t r = t / hx;
+        x = 2 * (int)(t - r * hx) + (c & 1);
+        y = 2 * (int)r + (c >> 1);
+        z = 0;
+    } else {
+        const int hy = a.Ly >> 1;
+        const int64_t r = t / hx;
+        x = 2 * (int)(t - r * hx) + (c & 1);
+        y = 2 * (int)(r % hy) + ((c >> 1) & 1);
+        z = 2 * (int)(r / hy) + (c >> 2);
+    }
+    const int64_t sxy = (int64_t)a.Lx * a.Ly;
+    const int64_t i = x + (int64_t)a.Lx * y + sxy * z;
+    const int32_t qi = a.q[i];
+    int32_t nv[G::M];
+    int64_t ni[G::M];
+    int same_old = 0;
+#pragma unroll
+    for (int k = 0; k < G::M; ++k) {
+        int dx, dy, dz;
+        G::off(k, dx, dy, dz);
+        const int xx = wrapi(x + dx, a.Lx), yy = wrapi(y + dy, a.Ly), zz = DIM == 3 ? wrapi(z + dz, a.Lz) : 0;
+        ni[k] = xx + (int64_t)a.Lx * yy + sxy * zz;
+        nv[k] = a.q[ni[k]];
+        same_old += nv[k] == qi;
+    }
+    if (same_old == G::M) return;
+    const uint4 u = draw(a.seed, (uint64_t)i, a.sweep, kTagSweep, (uint32_t)c);
+    const int kp = (int)__umulhi(u.x, (uint32_t)G::M);
+    int32_t qj = 0;
+    int64_t j = 0;
+#pragma unroll
+    for (int k = 0; k < G::M; ++k)
+        if (k == kp) { qj = nv[k]; j = ni[k]; }
+    if (qj == qi) return;
+    int same_new = 0;
+#pragma unroll
+    for (int k = 0; k < G::M; ++k) same_new += nv[k] == qj;
+    int32_t db = 0;
+    int32_t mpj = 0;
+    if (HASMP) mpj = a.mp[j];
+    if (FIELD == 1) db = tab(a.table, a.table_n, qj) - tab(a.table, a.table_n, qi);
+    if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, a.mp[i]);
+    const int32_t d = a.J * (same_old - same_new) + db;
+    if (metropolis(d, a.D, a.thr, u.y)) {
+        a.q[i] = qj;
+        if (HASMP) a.mp[i] = mpj;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused plane kernel.  One CTA = one TX x TY tile of one plane.  Window of
+// (TX+2H) x (TY+2H) sites with H = NP (the halo shrinks by one per phase).
+// ---------------------------------------------------------------------------
+struct PlaneArgs {
+    const int32_t* q_in;    // own plane, previous state
+    const int32_t* mp_in;
+    const int32_t* q_nb;    // z-neighbour planes (3D)
+    const int32_t* mp_nb;
+    int32_t* q_out;
+    int32_t* mp_out;
+    const int32_t* table;
+    uint32_t table_n;
+    const uint32_t* thr;
+    int32_t D, J;
+    uint64_t seed;
+    uint32_t sweep;
+    int Lx, Ly, Lz;
+    int zpar;               // 3D: parity of the planes handled by this launch
+    int tiles_x;
+};
+
+template <int NBR, int TX, int TY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
+    constexpr bool Z = NBR == 26;
+    constexpr int NP = NBR == 4 ? 2 : 4;  // in-plane colour phases
+    constexpr int H = NP;
+    constexpr int WX = TX + 2 * H, WY = TY + 2 * H, WN = WX * WY;
+    constexpr int M = NBR;
+    extern __shared__ int32_t smem[];
+    int32_t* s_q = smem;
+    int32_t* s_mp = smem + WN;                      // used when HASMP
+    int32_t* s_lo = smem + (HASMP ? 2 : 1) * WN;    // plane z-1 (3D)
+    int32_t* s_hi = s_lo + WN;                      // plane z+1 (3D)
+
+    const int tile = blockIdx.x;
+    const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+    const int x0 = tx * TX, y0 = ty * TY;
+    const int z = Z ? 2 * (int)blockIdx.y + a.zpar : 0;
+    const int zlo = Z ? wrapi(z - 1, a.Lz) : 0, zhi = Z ? wrapi(z + 1, a.Lz) : 0;
+    const int64_t sxy = (int64_t)a.Lx * a.Ly;
+    const int32_t* qp = a.q_in + sxy * z;
+    const int32_t* mpp = HASMP ? a.mp_in + sxy * z : nullptr;
+
+    for (int idx = threadIdx.x; idx < WN; idx += kThreads) {
+        const int ly = idx / WX, lx = idx - ly * WX;
+        const int gx = wrapi(x0 - H + lx, a.Lx), gy = wrapi(y0 - H + ly, a.Ly);
+        const int64_t o = gx + (int64_t)a.Lx * gy;
+        s_q[idx] = qp[o];
+        if (HASMP) s_mp[idx] = mpp[o];
+        if (Z) {
+            s_lo[idx] = a.q_nb[sxy * zlo + o];
+            s_hi[idx] = a.q_nb[sxy * zhi + o];
+        }
+    }
+    __syncthreads();
+
+    const int cz = Z ? 4 * a.zpar : 0;
+#pragma unroll 1
+    for (int p = 0; p < NP; ++p) {
+        const int lo = p + 1, hix = WX - p - 1, hiy = WY - p - 1;
+        int nx, ny, xs, ys;
+        if (NBR == 4) {
+            nx = (hix - lo + 1) >> 1;  // sites per row (upper bound)
+            ny = hiy - lo;
+            xs = ys = lo;
+        } else {
+            const int cx = p & 1, cy = p >> 1;
+            xs = lo + ((lo ^ cx) & 1);
+            ys = lo + ((lo ^ cy) & 1);
+            nx = (hix - xs + 1) >> 1;
+            ny = (hiy - ys + 1) >> 1;
+        }
+        const int n = nx * ny;
+        for (int s = threadIdx.x; s < n; s += kThreads) {
+            const int r = s / nx, k = s - r * nx;
+            int lx, ly;
+            if (NBR == 4) {
+                ly = ys + r;
+                lx = xs + ((xs + ly + p) & 1) + 2 * k;
+                if (lx >= hix) continue;
+            } else {
+                lx = xs + 2 * k;
+                ly = ys + 2 * r;
+            }
+            const int li = ly * WX + lx;
+            const int32_t qi = s_q[li];
+            int same_old = 0;
+            if (NBR == 4) {
+                same_old = (s_q[li + 1] == qi) + (s_q[li - 1] == qi) + (s_q[li + WX] == qi) + (s_q[li - WX] == qi);
+            } else {
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dx || dy) same_old += s_q[li + dy * WX + dx] == qi;
+                        if (Z) same_old += (s_lo[li + dy * WX + dx] == qi) + (s_hi[li + dy * WX + dx] == qi);
+                    }
+            }
+            if (same_old == M) continue;
+            const int gx = wrapi(x0 - H + lx, a.Lx), gy = wrapi(y0 - H + ly, a.Ly);
+            const int64_t gi = gx + (int64_t)a.Lx * gy + sxy * z;
+            const int colour = NBR == 4 ? p : cz + p;
+            const uint4 u = draw(a.seed, (uint64_t)gi, a.sweep, kTagSweep, (uint32_t)colour);
+            const int kp = (int)__umulhi(u.x, (uint32_t)M);
+            // neighbour kp: plane (-1, 0, +1) and in-plane offset
+            int dx, dy, dz;
+            if (NBR == 4) {
+                Geo<2, 4>::off(kp, dx, dy, dz);
+            } else if (NBR == 8) {
+                Geo<2, 8>::off(kp, dx, dy, dz);
+            } else {
+                Geo<3, 26>::off(kp, dx, dy, dz);
+            }
+            const int lj = li + dy * WX + dx;
+            const int32_t qj = dz == 0 ? s_q[lj] : (dz < 0 ? s_lo[lj] : s_hi[lj]);
+            if (qj == qi) continue;
+            int same_new = 0;
+            if (NBR == 4) {
+                same_new = (s_q[li + 1] == qj) + (s_q[li - 1] == qj) + (s_q[li + WX] == qj) + (s_q[li - WX] == qj);
+            } else {
+#pragma unroll
+                for (int ddy = -1; ddy <= 1; ++ddy)
+#pragma unroll
+                    for (int ddx = -1; ddx <= 1; ++ddx) {
+                        if (ddx || ddy) same_new += s_q[li + ddy * WX + ddx] == qj;
+                        if (Z) same_new += (s_lo[li + ddy * WX + ddx] == qj) + (s_hi[li + ddy * WX + ddx] == qj);
+                    }
+            }
+            int32_t mpj = 0;
+            if (HASMP) {
+                if (dz == 0) {
+                    mpj = s_mp[lj];
+                } else {
+                    const int jx = wrapi(gx + dx, a.Lx), jy = wrapi(gy + dy, a.Ly);
+                    const int jz = dz < 0 ? zlo : zhi;
+                    mpj = a.mp_nb[jx + (int64_t)a.Lx * jy + sxy * jz];
+                }
+            }
+            int32_t db = 0;
+            if (FIELD == 1) db = tab(a.table, a.table_n, qj) - tab(a.table, a.table_n, qi);
+            if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, s_mp[li]);
+            const int32_t d = a.J * (same_old - same_new) + db;
+            if (metropolis(d, a.D, a.thr, u.y)) {
+                s_q[li] = qj;
+                if (HASMP) s_mp[li] = mpj;
+            }
+        }
+        __syncthreads();
+    }
+
+    // write the core of the tile (skip the part of a ragged tile beyond the lattice)
+    int32_t* qo = a.q_out + sxy * z;
+    int32_t* mpo = HASMP ? a.mp_out + sxy * z : nullptr;
+    for (int idx = threadIdx.x; idx < TX * TY; idx += kThreads) {
+        const int cy = idx / TX, cx = idx - cy * TX;
+        const int gx = x0 + cx, gy = y0 + cy;
+        if (gx >= a.Lx || gy >= a.Ly) continue;
+        const int li = (cy + H) * WX + cx + H;
+        const int64_t o = gx + (int64_t)a.Lx * gy;
+        qo[o] = s_q[li];
+        if (HASMP) mpo[o] = s_mp[li];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host dispatch
+// ---------------------------------------------------------------------------
+template <int DIM, int NBR, int FIELD, bool HASMP>
+int launch_phase(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
+    PhaseArgs a;
+    a.q = h->q;
+    a.mp = h->mp;
+    a.table = h->table;
+    a.table_n = (uint32_t)h->table_n;
+    a.thr = h->thr;
+    a.D = h->D;
+    a.J = h->desc.J_fix;
+    a.seed = h->desc.seed;
+    a.sweep = sweep;
+    a.colour = colour;
+    a.Lx = (int)h->lat.L[0];
+    a.Ly = (int)h->lat.L[1];
+    a.Lz = (int)h->lat.L[2];
+    a.n_colour_sites = h->lat.N / Geo<DIM, NBR>::C;
+    const int64_t blocks = (a.n_colour_sites + kThreads - 1) / kThreads;
+    k_phase<DIM, NBR, FIELD, HASMP><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    HP_LAUNCH_CHECK("k_phase");
+    return HP_OK;
+}
+
+template <int DIM, int NBR>
+int phase_dispatch(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
+    const bool m = h->mp != nullptr;
+    switch (h->desc.field_mode) {
+        case HP_FIELD_NONE:
+            return m ? launch_phase<DIM, NBR, 0, true>(h, sweep, colour, s) : launch_phase<DIM, NBR, 0, false>(h, sweep, colour, s);
+        case HP_FIELD_GRAIN:
+            return m ? launch_phase<DIM, NBR, 1, true>(h, sweep, colour, s) : launch_phase<DIM, NBR, 1, false>(h, sweep, colour, s);
+        default:
+            return launch_phase<DIM, NBR, 2, true>(h, sweep, colour, s);
+    }
+}
+
+int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
+    const int dim = h->lat.dim, nbr = h->lat.nbr;
+    if (dim == 2 && nbr == 4) return phase_dispatch<2, 4>(h, sweep, colour, s);
+    if (dim == 2 && nbr == 8) return phase_dispatch<2, 8>(h, sweep, colour, s);
+    if (dim == 3 && nbr == 6) return phase_dispatch<3, 6>(h, sweep, colour, s);
+    return phase_dispatch<3, 26>(h, sweep, colour, s);
+}
+
+template <int NBR>
+struct PlaneTile {
+    static constexpr int TX = 64, TY = NBR == 26 ? 32 : 64;
+};
+
+template <int NBR, int FIELD, bool HASMP>
+int launch_plane(const PlaneArgs& a, int tiles, int planes, cudaStream_t s) {
+    constexpr int TX = PlaneTile<NBR>::TX, TY = PlaneTile<NBR>::TY;
+    constexpr int H = NBR == 4 ? 2 : 4;
+    constexpr int WN = (TX + 2 * H) * (TY + 2 * H);
+    constexpr int arrays = 1 + (HASMP ? 1 : 0) + (NBR == 26 ? 2 : 0);
+    const size_t smem = sizeof(int32_t) * WN * arrays;
+    auto fn = k_plane<NBR, TX, TY, FIELD, HASMP>;
+    static bool configured = false;  // per template instance
+    if (!configured) {
+        HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    fn<<<dim3((unsigned)tiles, (unsigned)planes), kThreads, smem, s>>>(a);
+    HP_LAUNCH_CHECK("k_plane");
+    return HP_OK;
+}
+
+template <int NBR>
+int plane_dispatch(hp_handle* h, const PlaneArgs& a, int tiles, int planes, cudaStream_t s) {
+    const bool m = h->mp != nullptr;
+    switch (h->desc.field_mode) {
+        case HP_FIELD_NONE:
+            return m ? launch_plane<NBR, 0, true>(a, tiles, planes, s) : launch_plane<NBR, 0, false>(a, tiles, planes, s);
+        case HP_FIELD_GRAIN:
+            return m ? launch_plane<NBR, 1, true>(a, tiles, planes, s) : launch_plane<NBR, 1, false>(a, tiles, planes, s);
+        default:
+            return launch_plane<NBR, 2, true>(a, tiles, planes, s);
+    }
+}
+
+int run_plane_kernel(hp_handle* h, const int32_t* q_in, const int32_t* mp_in, const int32_t* q_nb,
+                     const int32_t* mp_nb, int32_t* q_out, int32_t* mp_out, uint32_t sweep, int zpar,
+                     cudaStream_t s) {
+    PlaneArgs a;
+    a.q_in = q_in;
+    a.mp_in = mp_in;
+    a.q_nb = q_nb;
+    a.mp_nb = mp_nb;
+    a.q_out = q_out;
+    a.mp_out = mp_out;
+    a.table = h->table;
+    a.table_n = (uint32_t)h->table_n;
+    a.thr = h->thr;
+    a.D = h->D;
+    a.J = h->desc.J_fix;
+    a.seed = h->desc.seed;
+    a.sweep = sweep;
+    a.Lx = (int)h->lat.L[0];
+    a.Ly = (int)h->lat.L[1];
+    a.Lz = (int)h->lat.L[2];
+    a.zpar = zpar;
+    const int nbr = h->lat.nbr;
+    int TX, TY;
+    if (nbr == 4) { TX = PlaneTile<4>::TX; TY = PlaneTile<4>::TY; }
+    else if (nbr == 8) { TX = PlaneTile<8>::TX; TY = PlaneTile<8>::TY; }
+    else { TX = PlaneTile<26>::TX; TY = PlaneTile<26>::TY; }
+    a.tiles_x = (a.Lx + TX - 1) / TX;
+    const int tiles = a.tiles_x * ((a.Ly + TY - 1) / TY);
+    const int planes = nbr == 26 ? a.Lz / 2 : 1;
+    if (nbr == 4) return plane_dispatch<4>(h, a, tiles, planes, s);
+    if (nbr == 8) return plane_dispatch<8>(h, a, tiles, planes, s);
+    return plane_dispatch<26>(h, a, tiles, planes, s);
+}
+
+}  // namespace
+
+int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
+    const int nbr = h->lat.nbr;
+    const bool fused_ok = nbr != 6;
+    const bool fused = fused_ok && h->sweep_kernel != HP_SWEEP_PHASE;
+    if (!fused) {
+        for (int32_t t = 0; t < n_mcs; ++t)
+            for (int c = 0; c < h->lat.colours; ++c) {
+                const int rc = run_phase_kernel(h, (uint32_t)(h->sweep + t), c, s);
+                if (rc) return rc;
+            }
+        h->sweep += (uint64_t)n_mcs;
+        return HP_OK;
+    }
+    const bool m = h->mp != nullptr;
+    int32_t *qc = h->q, *mc = h->mp, *qa = h->q_alt, *ma = m ? h->mp_alt : nullptr;
+    for (int32_t t = 0; t < n_mcs; ++t) {
+        const uint32_t sw = (uint32_t)(h->sweep + t);
+        int rc;
+        if (nbr == 26) {
+            rc = run_plane_kernel(h, qc, mc, qc, mc, qa, ma, sw, 0, s);
+            if (rc) return rc;
+            rc = run_plane_kernel(h, qc, mc, qa, ma, qa, ma, sw, 1, s);
+        } else {
+            rc = run_plane_kernel(h, qc, mc, nullptr, nullptr, qa, ma, sw, 0, s);
+        }
+        if (rc) return rc;
+        int32_t* tq = qc; qc = qa; qa = tq;
+        int32_t* tm = mc; mc = ma; ma = tm;
+    }
+    if (qc != h->q) {
+        const size_t bytes = sizeof(int32_t) * (size_t)h->lat.N;
+        HP_CUDA(cudaMemcpyAsync(h->q, qc, bytes, cudaMemcpyDeviceToDevice, s));
+        if (m) HP_CUDA(cudaMemcpyAsync(h->mp, mc, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    h->sweep += (uint64_t)n_mcs;
+    return HP_OK;
+}
+
+}  // namespace hp
