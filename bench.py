@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: Potts site-updates/s of the hybrid Monte Carlo hot path on GB300.
+
+Workload (default): 2D 4096x4096 periodic lattice, Moore 8-neighbour 4-colour
+sweep, 10^4 Voronoi grains with SO(3)-uniform cubic-Ni orientations, per-grain
+field = elastic energy under uniaxial 100 MPa + dislocation energy weighted by
+the max Schmid factor, kT = 0.6, 1000 MCS.  One step = the whole job on
+synthetic input already in HBM: Voronoi initialisation, closed-form field,
+1000 MCS, grain counts and texture histogram.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
+rank runs its own independent lattice (its own seed): weak scaling, no
+collective on the data path; the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1007_3509_gb300 import synth  # noqa: E402
+
+W = synth.W2D_MOORE
+BYTES_PER_SITE_UPDATE = 8  # q read + q write per site per MCS; field looked up per grain (L1/L2)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--mcs", type=int, default=W.n_mcs, help="MCS per step (default: the workload's 1000)")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+class Job:
+    """Device-resident buffers of one lattice of the workload."""
+
+    def __init__(self, torch, hm, seed, mcs):
+        self.torch, self.hm, self.mcs = torch, hm, mcs
+        L, G = W.L, W.G
+        self.N = int(np.prod(L))
+        dev = "cuda"
+        self.lat = hm.Lattice(2, L, W.nbr, int(256 * W.J), seed, G, hm.FIELD_GRAIN)
+        self.q = torch.empty(self.N, dtype=torch.int32, device=dev)
+        self.lat.hp_bind(self.q)
+        self.quat = torch.empty(G, 4, dtype=torch.float32, device=dev)
+        self.bgrain = torch.empty(G, dtype=torch.int32, device=dev)
+        self.counts = torch.empty(G, dtype=torch.int64, device=dev)
+        self.alive = torch.empty(1, dtype=torch.int32, device=dev)
+        self.bins = torch.empty(2 * G, dtype=torch.int32, device=dev)
+        self.hist = torch.empty(24, dtype=torch.int64, device=dev)
+        thr, D = hm.hp_build_threshold_table(W.kT)
+        self.lat.hp_set_threshold_table(thr, D)
+        self.lat.hp_set_field(self.bgrain)
+        self.C = [synth.NI_BJ[k] for k in ("C11", "C12", "C44")]
+
+    def field(self):
+        self.hm.hp_grain_field(self.quat, *self.C, W.sigma, W.k_disl, W.energy_scale, self.bgrain)
+
+    def measure(self):
+        self.lat.hp_grain_counts(self.counts, self.alive)
+        self.hm.hp_texture(W.G, self.hm.ORIENT_SO3, self.quat, self.counts, self.bins, self.hist)
+
+    def step(self, ev_sweep=None):
+        """Whole job: init, field, sweep, measure."""
+        self.lat.hp_init_voronoi(self.hm.ORIENT_SO3, self.quat)
+        self.field()
+        self.lat.hp_set_sweep_counter(0)
+        if ev_sweep:
+            ev_sweep[0].record()
+        self.lat.hp_sweep(self.mcs)
+        if ev_sweep:
+            ev_sweep[1].record()
+        self.measure()
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    hm.lib()
+    job = Job(torch, hm, W.seed + rank, args.mcs)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        job.step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local_rank)
+    launches0 = hm.hp_kernel_launches()
+    step_ms, sweep_ms = [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        job.step((s0, s1))
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        sweep_ms.append(s0.elapsed_time(s1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = hm.hp_kernel_launches() - launches0
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    max_ms = float(t.item())
+    site_updates = job.N * args.mcs * args.steps * world
+    value = site_updates / (max_ms / 1e3)
+
+    # dominant kernel: one fused-plane launch per MCS over N sites
+    per_launch_s = statistics.mean(sweep_ms) / 1e3 / args.mcs
+    achieved = BYTES_PER_SITE_UPDATE * job.N / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "kernel": "k_plane<8> (fused 4-colour MCS)", "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
+            "sweep_site_updates_per_s": round(job.N / per_launch_s, 1)}
+    traffic = os.environ.get("HP_SWEEP_TRAFFIC_BYTES")
+    if traffic:
+        roof["traffic"] = float(traffic)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(torch, hm, job, args)
+    secondary = None
+    if not args.no_secondary and rank == 0:
+        secondary = run_secondary(torch, hm)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(target_s=12.0)
+    if rank != 0:
+        return
+    line = {
+        "metric": "Potts site-updates/s",
+        "value": round(value, 1),
+        "unit": "site-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(max_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (seeded Voronoi polycrystal, SO(3)-uniform orientations)",
+        "config": {"workload": W.name, "lattice": list(W.L), "nbr": W.nbr, "colours": 4, "grains": W.G,
+                   "kT": W.kT, "mcs_per_step": args.mcs, "field": "per-grain closed form (100 MPa, Ni)",
+                   "step": "voronoi init + field + sweep + counts/texture", "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "secondary": secondary,
+    }
+    print(json.dumps(line))
+
+
+def run_e2e(torch, hm, job, args):
+    """Same metric through the public API with host buffers: pinned H2D of the
+    initial lattice and orientations, field + sweep + measure, D2H of the final
+    lattice, counts and histogram, every step."""
+    G, N = W.G, job.N
+    job.lat.hp_init_voronoi(hm.ORIENT_SO3, job.quat)
+    h_q = job.q.cpu().pin_memory()
+    h_quat = job.quat.cpu().pin_memory()
+    o_q = torch.empty(N, dtype=torch.int32).pin_memory()
+    o_counts = torch.empty(G, dtype=torch.int64).pin_memory()
+    o_hist = torch.empty(24, dtype=torch.int64).pin_memory()
+
+    def one():
+        job.q.copy_(h_q, non_blocking=True)
+        job.quat.copy_(h_quat, non_blocking=True)
+        job.field()
+        job.lat.hp_set_sweep_counter(0)
+        job.lat.hp_sweep(args.mcs)
+        job.measure()
+        o_q.copy_(job.q, non_blocking=True)
+        o_counts.copy_(job.counts, non_blocking=True)
+        o_hist.copy_(job.hist, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    ms = []
+    steps = max(2, min(args.steps, 3))
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        one()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    per = statistics.mean(ms) / 1e3
+    h2d = h_q.numel() * 4 + h_quat.numel() * 4
+    d2h = o_q.numel() * 4 + o_counts.numel() * 8 + o_hist.numel() * 8
+    return {"value": round(N * args.mcs / per, 1), "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(per * 1e3, 3)}
+
+
+def run_secondary(torch, hm):
+    """The 3D 512^3 26-neighbour 8-colour sweep with a per-material-point field
+    (two fused launches per MCS), for the HBM roofline of the 3D path."""
+    try:
+        L = (512, 512, 512)
+        N = 512 ** 3
+        lat = hm.Lattice(3, L, 26, 256, 1002, 200_000, hm.FIELD_POINT)
+        q = torch.empty(N, dtype=torch.int32, device="cuda")
+        mp = torch.empty(N, dtype=torch.int32, device="cuda")
+        lat.hp_bind(q, mp)
+        lat.hp_init_voronoi(hm.ORIENT_SO3, None)
+        bmp = torch.randint(0, 30, (N,), dtype=torch.int32, device="cuda")
+        lat.hp_set_field(bmp)
+        thr, D = hm.hp_build_threshold_table(0.7)
+        lat.hp_set_threshold_table(thr, D)
+        lat.hp_sweep(4)
+        torch.cuda.synchronize()
+        n = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lat.hp_sweep(n)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3
+        rate = N * n / s
+        bytes_per = 20  # q, mp read + write (16 B) + one field read per site (4 B)
+        peak, _ = peaks()
+        lat.close()
+        del q, mp, bmp
+        torch.cuda.empty_cache()
+        return {"workload": "3d-512-moore26-point-field", "site_updates_per_s": round(rate, 1),
+                "bytes_per_site_update": bytes_per, "achieved_gbs": round(rate * bytes_per / 1e9, 1),
+                "frac_of_measured_hbm": round(rate * bytes_per / 1e9 / peak, 4), "mcs_timed": n}
+    except Exception as e:  # secondary numbers must not break the main line
+        return {"error": str(e)[:200]}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_job(L, G, mcs, seed):
+    """The oracle running the same job on a smaller lattice of the same grain
+    density: Voronoi, closed-form field, mcs Monte Carlo steps, counts."""
+    import oracle
+    t0 = time.perf_counter()
+    q, _ = oracle.voronoi(2, L, G, seed)
+    quat = oracle.orientations(G, seed, 1)
+    Cc = np.array([synth.NI_BJ[k] for k in ("C11", "C12", "C44")])
+    _, _, _, b = oracle.grain_field(quat, Cc, W.sigma, W.k_disl, W.energy_scale)
+    thr, D = oracle.threshold_table(W.kT)
+    q2, _, _, _ = oracle.sweep(2, L, W.nbr, int(256 * W.J), seed, 0, mcs, thr, D, q, b[q], None)
+    counts, alive = oracle.grain_counts(q2, G)
+    bins, _ = oracle.grain_bins(quat, 1)
+    oracle.histogram(counts, bins, 1)
+    dt = time.perf_counter() - t0
+    return int(np.prod(L)) * mcs, dt
+
+
+SAMPLE_L = (1024, 1024)
+SAMPLE_G = 625  # same sites per grain as 4096^2 / 10^4
+
+
+def cpu_baseline_sample(target_s=12.0):
+    mcs = 60
+    n, dt = oracle_job(SAMPLE_L, SAMPLE_G, mcs, W.seed)
+    return {"value": round(n / dt, 1), "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{SAMPLE_L[0]}x{SAMPLE_L[1]} lattice, {SAMPLE_G} grains (same density), {mcs} MCS, "
+                      f"whole job (voronoi, field, sweep, counts/texture), single thread", "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    mcs = 40
+    for _ in range(args.warmup):
+        oracle_job((256, 256), 39, 4, W.seed)
+    tot_n, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = oracle_job(SAMPLE_L, SAMPLE_G, mcs, W.seed)
+        tot_n += n
+        tot_s += dt
+    v = tot_n / tot_s
+    line = {
+        "metric": "Potts site-updates/s", "value": round(v, 1), "unit": "site-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_s / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": W.name, "lattice": list(W.L), "nbr": W.nbr, "grains": W.G, "kT": W.kT,
+                   "mcs_per_step": W.n_mcs, "parallelism": "cpu oracle"},
+        "cpu_baseline": {"value": round(v, 1), "unit": "site-updates/s", "kind": "oracle", "cores": 1,
+                         "sample": f"each step: {SAMPLE_L[0]}x{SAMPLE_L[1]}, {SAMPLE_G} grains, {mcs} MCS whole job"},
+        "e2e": {"value": round(v, 1), "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,10 @@ HP_API const char* hp_last_error_message(void);
 /* Library build/version string (never NULL). */
 HP_API const char* hp_version(void);
 
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all threads, all handles); for accounting in benchmarks.                  */
+HP_API int hp_kernel_launches(uint64_t* out);
+
 /* Create a lattice handle.  Validates the descriptor (Sec. 4: square or cubic
  * lattice, M neighbours; colour count follows from nbr: 2 for 4/6, 4 for 2D-8,
  * 8 for 3D-26).  No device memory is touched.                                */

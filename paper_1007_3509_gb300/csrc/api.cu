@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -11,6 +12,9 @@
 namespace hp {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int set_error(int code, const std::string& msg) {
     g_last_error = msg;
@@ -45,6 +49,12 @@ using namespace hp;
 extern "C" const char* hp_last_error_message(void) { return g_last_error.c_str(); }
 
 extern "C" const char* hp_version(void) { return "hmcpotts 0.1 sm_103a"; }
+
+extern "C" int hp_kernel_launches(uint64_t* out) {
+    if (!out) return set_error(HP_ERR_ARG, "hp_kernel_launches: null argument");
+    *out = g_launches.load(std::memory_order_relaxed);
+    return HP_OK;
+}
 
 extern "C" int hp_create(const hp_desc* d, hp_handle** out) {
     if (!d || !out) return set_error(HP_ERR_ARG, "hp_create: null argument");
@@ -184,6 +194,7 @@ extern "C" int hp_set_sweep_counter(hp_handle* h, uint64_t v) {
 extern "C" int hp_philox(uint64_t seed, const uint32_t* ctr, int64_t n, uint32_t* out, void* stream) {
     if (!ctr || !out || n < 0) return set_error(HP_ERR_ARG, "hp_philox: bad arguments");
     if (n == 0) return HP_OK;
+    ::hp::count_launch();
     k_philox<<<(unsigned)((n + 255) / 256), 256, 0, as_stream(stream)>>>(seed, reinterpret_cast<const uint4*>(ctr), n,
                                                                          reinterpret_cast<uint4*>(out));
     HP_LAUNCH_CHECK("k_philox");

@@ -32,6 +32,9 @@ int cuda_error(cudaError_t e, const char* what);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Process-wide count of kernel launches issued by this library.
+void count_launch();
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11).  Counter words: unit lo, unit hi,
 // step, tag << 24 | sub.  Key: seed lo, seed hi.

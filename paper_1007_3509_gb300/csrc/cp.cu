@@ -261,6 +261,7 @@ using namespace hp;
 extern "C" int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream) {
     if (!prm || !st || st->P < 1 || !st->eps_p || !st->gamma || !st->g)
         return set_error(HP_ERR_ARG, "hp_cp_reset: bad arguments");
+    ::hp::count_launch();
     k_cp_reset<<<(unsigned)((st->P + 255) / 256), 256, 0, as_stream(stream)>>>(st->P, st->eps_p, st->gamma, st->g,
                                                                                (float)prm->tau0);
     HP_LAUNCH_CHECK("k_cp_reset");
@@ -283,6 +284,7 @@ extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t*
     a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t0; a.n_incr = n_incr; a.P = st->P;
     a.eps_p = st->eps_p; a.gamma = st->gamma; a.g = st->g;
     a.sigma = sigma; a.w = w; a.erho = erho; a.b = b;
+    ::hp::count_launch();
     k_cp<<<(unsigned)((st->P + kT - 1) / kT), kT, 0, as_stream(stream)>>>(a);
     HP_LAUNCH_CHECK("k_cp");
     return HP_OK;

@@ -175,6 +175,7 @@ extern "C" int hp_grain_field(int32_t G, const float* quat, double C11, double C
     a.b = b_out;
     a.w = w_out;
     a.mmax = mmax_out;
+    ::hp::count_launch();
     k_grain_field<<<(G + kT - 1) / kT, kT, 0, as_stream(stream)>>>(a);
     HP_LAUNCH_CHECK("k_grain_field");
     return HP_OK;
@@ -190,10 +191,12 @@ extern "C" int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, vo
     HP_CUDA(cudaMallocAsync((void**)&bad, sizeof(int32_t), s));
     cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
     const int64_t threads = (h->lat.N + kSeg - 1) / kSeg;
+    ::hp::count_launch();
     k_counts<<<(unsigned)((threads + kT - 1) / kT), kT, 0, s>>>(h->q, h->lat.N, G,
                                                                 reinterpret_cast<unsigned long long*>(counts), bad);
     if (alive) {
         cudaMemsetAsync(alive, 0, sizeof(int32_t), s);
+        ::hp::count_launch();
         k_alive<<<(G + kT - 1) / kT, kT, 0, s>>>(reinterpret_cast<const unsigned long long*>(counts), G, alive);
     }
     int32_t nbad = 0;
@@ -210,10 +213,12 @@ extern "C" int hp_texture(int32_t G, int32_t orient_kind, const float* orient, c
     if (G < 1 || !orient || !bins || (orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_SO3))
         return set_error(HP_ERR_ARG, "hp_texture: bad arguments");
     cudaStream_t s = as_stream(stream);
+    ::hp::count_launch();
     k_bins<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, orient, bins);
     if (hist && counts) {
         const int nb = orient_kind == HP_ORIENT_ANGLE ? 90 : 24;
         HP_CUDA(cudaMemsetAsync(hist, 0, sizeof(int64_t) * nb, s));
+        ::hp::count_launch();
         k_hist<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, bins,
                                                  reinterpret_cast<const unsigned long long*>(counts),
                                                  reinterpret_cast<unsigned long long*>(hist));

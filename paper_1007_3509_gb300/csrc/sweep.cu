@@ -361,6 +361,7 @@ int launch_phase(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     a.Lz = (int)h->lat.L[2];
     a.n_colour_sites = h->lat.N / Geo<DIM, NBR>::C;
     const int64_t blocks = (a.n_colour_sites + kThreads - 1) / kThreads;
+    ::hp::count_launch();
     k_phase<DIM, NBR, FIELD, HASMP><<<(unsigned)blocks, kThreads, 0, s>>>(a);
     HP_LAUNCH_CHECK("k_phase");
     return HP_OK;
@@ -405,6 +406,7 @@ int launch_plane(const PlaneArgs& a, int tiles, int planes, cudaStream_t s) {
         HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
+    ::hp::count_launch();
     fn<<<dim3((unsigned)tiles, (unsigned)planes), kThreads, smem, s>>>(a);
     HP_LAUNCH_CHECK("k_plane");
     return HP_OK;

@@ -177,6 +177,7 @@ __global__ void k_orient(int32_t G, uint64_t seed, int32_t kind, float* out) {
 int orientations_run(int32_t G, uint64_t seed, int32_t kind, float* orient, cudaStream_t s) {
     if (G < 1 || !orient || (kind != HP_ORIENT_ANGLE && kind != HP_ORIENT_SO3))
         return set_error(HP_ERR_ARG, "hp_orientations: bad arguments");
+    ::hp::count_launch();
     k_orient<<<(G + kT - 1) / kT, kT, 0, s>>>(G, seed, kind, orient);
     HP_LAUNCH_CHECK("k_orient");
     return HP_OK;
@@ -228,7 +229,9 @@ int voronoi_run(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_
         const int gb = (G + kT - 1) / kT;
         for (uint32_t round = 0;; ++round) {
             if ((e = cudaMemsetAsync(n_left, 0, sizeof(int32_t), s))) break;
+            ::hp::count_launch();
             k_seed_claim<<<gb, kT, 0, s>>>(h->q, pos, G, h->desc.seed, round, N);
+            ::hp::count_launch();
             k_seed_resolve<<<gb, kT, 0, s>>>(h->q, pos, G, h->desc.seed, round, N, n_left);
             int32_t left = 0;
             if ((e = cudaMemcpyAsync(&left, n_left, sizeof(int32_t), cudaMemcpyDeviceToHost, s))) break;
@@ -239,13 +242,18 @@ int voronoi_run(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_
         if (e || rc) break;
         if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ncell, s))) break;
         if ((e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * ncell, s))) break;
+        ::hp::count_launch();
         k_cell_count<<<gb, kT, 0, s>>>(pos, G, c, cnt, xyz);
+        ::hp::count_launch();
         k_scan<<<1, 1024, 0, s>>>(cnt, start, (int32_t)ncell);
+        ::hp::count_launch();
         k_cell_scatter<<<gb, kT, 0, s>>>(xyz, G, start, cursor, list);
         const int64_t nb = (N + kT - 1) / kT;
+        ::hp::count_launch();
         k_assign<<<(unsigned)nb, kT, 0, s>>>(h->q, h->mp, N, c, start, list);
         if ((e = cudaGetLastError())) break;
         if (orient) {
+            ::hp::count_launch();
             k_orient<<<gb, kT, 0, s>>>(G, h->desc.seed, orient_kind, orient);
             if ((e = cudaGetLastError())) break;
         }

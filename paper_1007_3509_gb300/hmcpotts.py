@@ -49,6 +49,7 @@ class hp_cp_state(C.Structure):
 _SIGS = {
     "hp_last_error_message": ([], C.c_char_p),
     "hp_version": ([], C.c_char_p),
+    "hp_kernel_launches": ([C.POINTER(C.c_uint64)], C.c_int),
     "hp_create": ([C.POINTER(hp_desc), C.POINTER(C.c_void_p)], C.c_int),
     "hp_destroy": ([C.c_void_p], C.c_int),
     "hp_bind": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -117,6 +118,12 @@ def _stream(stream):
 
 def version() -> str:
     return lib().hp_version().decode()
+
+
+def hp_kernel_launches() -> int:
+    v = C.c_uint64(0)
+    _check(lib().hp_kernel_launches(C.byref(v)))
+    return v.value
 
 
 def hp_build_threshold_table(kT: float, zero_rule: int = 0, cap: int = 1 << 16):
