@@ -105,6 +105,25 @@ HP_API int hp_bind(hp_handle* h, int32_t* q, int32_t* mp);
  * may be NULL).  Synchronises `stream` once per seeding round.               */
 HP_API int hp_init_voronoi(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, void* stream);
 
+/* Same tessellation as hp_init_voronoi (bit-identical q, seed_pos, orient),
+ * but it allocates no device memory: no cudaMalloc, cudaFree or allocating
+ * library routine is called.  The paper has no counterpart; this entry point
+ * exists for callers that cannot allocate while they run, such as a process
+ * whose device memory is all pre-reserved by another allocator, or a
+ * steady-state loop that must never enter the allocator.
+ * Scratch (seed coordinates, cell lists and counters) lives in one file-scope
+ * device array of HP_VORONOI_STATIC_BYTES (16 MiB) that every GPU loading the
+ * library holds until exit; G above HP_VORONOI_STATIC_MAX_GRAINS is rejected
+ * with HP_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and each
+ * call clears what it needs, so calls that overlap on the GPU (concurrent
+ * streams, several host threads) race and must be serialised by the caller.
+ * Like hp_init_voronoi it synchronises `stream` once per seeding round.       */
+#define HP_VORONOI_STATIC_BYTES (16u << 20)
+#define HP_VORONOI_STATIC_MAX_GRAINS 262144
+HP_API int hp_init_voronoi_static(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, void* stream);
+
 /* Orientations only (same draws as hp_init_voronoi).                          */
 HP_API int hp_orientations(int32_t G, uint64_t seed, int32_t orient_kind, float* orient, void* stream);
 

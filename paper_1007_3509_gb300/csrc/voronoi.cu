@@ -15,6 +15,8 @@
 // outside the scanned rings can have (wmin = narrowest cell width).
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace hp {
@@ -264,3 +266,127 @@ int voronoi_run(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_
 }
 
 }  // namespace hp
+
+// ---------------------------------------------------------------------------
+// Voronoi initialisation without any device allocation.
+//
+// For callers that cannot allocate device memory while they run -- e.g. a
+// process whose device memory is entirely pre-reserved by another allocator,
+// or a steady-state loop that must never enter cudaMalloc/cudaFree -- the
+// scratch of the tessellation (seed coordinates, cell lists, cell counters,
+// the round counter) lives in one file-scope device array of fixed size.
+// The array exists on every GPU that loads this library, until exit.
+// ---------------------------------------------------------------------------
+namespace hp {
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_vor_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device.  The array's
+// name is only a host-side stand-in; its device address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+int static_scratch(void** out) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(HP_ERR_ARG, "hp_init_voronoi_static: device ordinal too large");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_vor_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "hp_init_voronoi_static: cudaGetSymbolAddress");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return HP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace hp
+
+extern "C" int hp_init_voronoi_static(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos,
+                                      void* stream) {
+    using namespace hp;
+    if (!h) return set_error(HP_ERR_ARG, "hp_init_voronoi_static: null handle");
+    if (!h->q) return set_error(HP_ERR_STATE, "hp_init_voronoi_static: no lattice bound");
+    if (orient && orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_SO3)
+        return set_error(HP_ERR_ARG, "hp_init_voronoi_static: bad orient_kind");
+    const int32_t G = h->desc.n_grains;
+    const int64_t N = h->lat.N;
+    if (G < 1 || G > N) return set_error(HP_ERR_ARG, "hp_init_voronoi_static: need 1 <= G <= N");
+    if (G > HP_VORONOI_STATIC_MAX_GRAINS)
+        return set_error(HP_ERR_ARG, "hp_init_voronoi_static: more grains than the static scratch holds "
+                                     "(HP_VORONOI_STATIC_MAX_GRAINS); use hp_init_voronoi");
+    if (N >= (int64_t)1 << 32) return set_error(HP_ERR_ARG, "hp_init_voronoi_static: lattice too large (N >= 2^32)");
+    cudaStream_t s = as_stream(stream);
+    Cells c;
+    c.dim = h->lat.dim;
+    for (int d = 0; d < 3; ++d) c.L[d] = (int)h->lat.L[d];
+    const double per = pow(2.0 * (double)N / (double)G, 1.0 / c.dim);
+    int64_t ncell = 1;
+    c.wmin = INT32_MAX;
+    for (int d = 0; d < 3; ++d) {
+        if (d >= c.dim) { c.nc[d] = 1; continue; }
+        int n = (int)floor((double)c.L[d] / per);
+        n = n < 1 ? 1 : n;
+        c.nc[d] = n;
+        ncell *= n;
+        const int w = c.L[d] / n;
+        c.wmin = w < c.wmin ? w : c.wmin;
+    }
+    // carve the static scratch
+    void* base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc) return rc;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { void* p = (unsigned char*)base + off; off += align256(bytes); return p; };
+    int64_t* pos = seed_pos ? seed_pos : (int64_t*)take(sizeof(int64_t) * G);
+    int4* xyz = (int4*)take(sizeof(int4) * G);
+    int4* list = (int4*)take(sizeof(int4) * G);
+    int32_t* cnt = (int32_t*)take(sizeof(int32_t) * ncell);
+    int32_t* start = (int32_t*)take(sizeof(int32_t) * (ncell + 1));
+    int32_t* cursor = (int32_t*)take(sizeof(int32_t) * ncell);
+    int32_t* n_left = (int32_t*)take(sizeof(int32_t));
+    if (off > kStaticScratchBytes)
+        return set_error(HP_ERR_ARG, "hp_init_voronoi_static: scratch layout exceeds the static array");
+
+    // everything that must start at zero (or -1) is cleared here on every call
+    HP_CUDA(cudaMemsetAsync(h->q, 0x7F, sizeof(int32_t) * N, s));
+    HP_CUDA(cudaMemsetAsync(pos, 0xFF, sizeof(int64_t) * G, s));
+    const int gb = (G + kT - 1) / kT;
+    for (uint32_t round = 0;; ++round) {
+        HP_CUDA(cudaMemsetAsync(n_left, 0, sizeof(int32_t), s));
+        ::hp::count_launch();
+        k_seed_claim<<<gb, kT, 0, s>>>(h->q, pos, G, h->desc.seed, round, N);
+        ::hp::count_launch();
+        k_seed_resolve<<<gb, kT, 0, s>>>(h->q, pos, G, h->desc.seed, round, N, n_left);
+        int32_t left = 0;
+        HP_CUDA(cudaMemcpyAsync(&left, n_left, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HP_CUDA(cudaStreamSynchronize(s));
+        if (left == 0) break;
+        if (round > (1u << 20)) return set_error(HP_ERR_STATE, "hp_init_voronoi_static: seeding did not converge");
+    }
+    HP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ncell, s));
+    HP_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * ncell, s));
+    ::hp::count_launch();
+    k_cell_count<<<gb, kT, 0, s>>>(pos, G, c, cnt, xyz);
+    ::hp::count_launch();
+    k_scan<<<1, 1024, 0, s>>>(cnt, start, (int32_t)ncell);
+    ::hp::count_launch();
+    k_cell_scatter<<<gb, kT, 0, s>>>(xyz, G, start, cursor, list);
+    const int64_t nb = (N + kT - 1) / kT;
+    ::hp::count_launch();
+    k_assign<<<(unsigned)nb, kT, 0, s>>>(h->q, h->mp, N, c, start, list);
+    if (orient) {
+        ::hp::count_launch();
+        k_orient<<<gb, kT, 0, s>>>(G, h->desc.seed, orient_kind, orient);
+    }
+    HP_LAUNCH_CHECK("hp_init_voronoi_static");
+    return HP_OK;
+}

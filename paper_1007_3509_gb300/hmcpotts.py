@@ -54,6 +54,7 @@ _SIGS = {
     "hp_destroy": ([C.c_void_p], C.c_int),
     "hp_bind": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_init_voronoi": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_init_voronoi_static": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_orientations": ([C.c_int32, C.c_uint64, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "hp_set_field": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "hp_build_threshold_table": ([C.c_double, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
@@ -204,6 +205,11 @@ class Lattice:
 
     def hp_init_voronoi(self, orient_kind=ORIENT_ANGLE, orient=None, seed_pos=None, stream=None):
         _check(lib().hp_init_voronoi(self._h, int(orient_kind), _ptr(orient), _ptr(seed_pos), _stream(stream)))
+
+    def hp_init_voronoi_static(self, orient_kind=ORIENT_ANGLE, orient=None, seed_pos=None, stream=None):
+        """Same as hp_init_voronoi, with no device allocation (fixed-size static scratch)."""
+        _check(lib().hp_init_voronoi_static(self._h, int(orient_kind), _ptr(orient), _ptr(seed_pos),
+                                            _stream(stream)))
 
     def hp_set_field(self, table):
         _check(lib().hp_set_field(self._h, _ptr(table), int(table.numel())))
