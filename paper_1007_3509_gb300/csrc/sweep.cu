@@ -176,8 +176,20 @@ __global__ void __launch_bounds__(kThreads) k_phase(PhaseArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused plane kernel.  One CTA = one TX x TY tile of one plane.  Window of
-// (TX+2H) x (TY+2H) sites with H = NP (the halo shrinks by one per phase).
+// Fused plane kernel.  One CTA = one TX x TY tile of one plane.  The window
+// holds the tile plus a halo of H = 4 sites (at least one site per colour
+// phase run here: 2 for the 4-neighbour lattice, 4 for Moore planes).
+//
+// Shared layout: each window row is split by x parity, element (lx, ly) at
+// [lx & 1][ly][lx >> 1].  Sites of one colour then sit at unit stride, and so
+// do their x neighbours, so warps read shared memory without bank conflicts.
+//
+// Each phase has two stages.  A: every site of the colour in the still-valid
+// region counts its neighbours equal to itself; a site whose neighbours all
+// match cannot change, the others are appended to a shared queue.  B: the
+// queued sites draw their random numbers and run the Metropolis update, with
+// every lane of every warp busy.  The order inside a phase is irrelevant: no
+// two sites of one colour are neighbours.
 // ---------------------------------------------------------------------------
 struct PlaneArgs {
     const int32_t* q_in;    // own plane, previous state
@@ -195,20 +207,71 @@ struct PlaneArgs {
     int Lx, Ly, Lz;
     int zpar;               // 3D: parity of the planes handled by this launch
     int tiles_x;
+    int fast;               // 1: window narrower than the lattice (wrap by one add)
+    int vec;                // 1: fast and Lx % 4 == 0 (16-byte row chunks)
 };
 
-template <int NBR, int TX, int TY, int FIELD, bool HASMP>
+__device__ __forceinline__ int wrap1(int a, int L) {
+    a += a < 0 ? L : 0;
+    return a - (a >= L ? L : 0);
+}
+
+template <int NBR, int TY>
+struct PlaneCfg {
+    static constexpr int H = 4;
+    static constexpr int WX = 128, WXH = 64, TX = WX - 2 * H;
+    static constexpr int WY = TY + 2 * H;
+    static constexpr int PL = WY * WXH;                  // one parity half of a window plane
+    static constexpr int NP = NBR == 4 ? 2 : 4;          // colour phases in a plane
+    static constexpr bool Z = NBR == 26;
+    static constexpr int QCAP = WXH * WY;                // queue capacity (>= sites of one colour)
+    static constexpr int planes = Z ? 3 : 1;
+    static size_t smem(bool hasmp) {
+        return sizeof(int32_t) * (size_t)(2 * PL) * (planes + (hasmp ? 1 : 0)) + sizeof(uint32_t) * QCAP +
+               sizeof(int) * 8;
+    }
+};
+
+// Load a window plane (q, and optionally mp) into the parity-split layout.
+template <class Cfg>
+__device__ __forceinline__ void load_window(const PlaneArgs& a, const int32_t* __restrict__ src,
+                                            int32_t* __restrict__ dst, int x0, int y0) {
+    constexpr int WX = Cfg::WX, WXH = Cfg::WXH, WY = Cfg::WY, PL = Cfg::PL, H = Cfg::H;
+    if (a.vec) {
+        constexpr int CH = WX / 4;  // 16-byte chunks per row
+        for (int idx = threadIdx.x; idx < CH * WY; idx += kThreads) {
+            const int ly = idx / CH, c = idx - ly * CH;
+            const int gy = wrap1(y0 - H + ly, a.Ly);
+            const int gx = wrap1(x0 - H + 4 * c, a.Lx);
+            const int4 v = __ldg(reinterpret_cast<const int4*>(src + gx + (int64_t)a.Lx * gy));
+            int32_t* row = dst + ly * WXH + 2 * c;
+            *reinterpret_cast<int2*>(row) = make_int2(v.x, v.z);
+            *reinterpret_cast<int2*>(row + PL) = make_int2(v.y, v.w);
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < WX * WY; idx += kThreads) {
+            const int ly = idx / WX, lx = idx - ly * WX;
+            const int gx = a.fast ? wrap1(x0 - H + lx, a.Lx) : wrapi(x0 - H + lx, a.Lx);
+            const int gy = a.fast ? wrap1(y0 - H + ly, a.Ly) : wrapi(y0 - H + ly, a.Ly);
+            dst[(lx & 1) * PL + ly * WXH + (lx >> 1)] = src[gx + (int64_t)a.Lx * gy];
+        }
+    }
+}
+
+template <int NBR, int TY, int FIELD, bool HASMP>
 __global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
-    constexpr bool Z = NBR == 26;
-    constexpr int NP = NBR == 4 ? 2 : 4;  // in-plane colour phases
-    constexpr int H = NP;
-    constexpr int WX = TX + 2 * H, WY = TY + 2 * H, WN = WX * WY;
+    using Cfg = PlaneCfg<NBR, TY>;
+    constexpr int H = Cfg::H, WX = Cfg::WX, WXH = Cfg::WXH, WY = Cfg::WY, PL = Cfg::PL, TX = Cfg::TX;
+    constexpr int NP = Cfg::NP;
+    constexpr bool Z = Cfg::Z;
     constexpr int M = NBR;
-    extern __shared__ int32_t smem[];
+    extern __shared__ __align__(16) int32_t smem[];
     int32_t* s_q = smem;
-    int32_t* s_mp = smem + WN;                      // used when HASMP
-    int32_t* s_lo = smem + (HASMP ? 2 : 1) * WN;    // plane z-1 (3D)
-    int32_t* s_hi = s_lo + WN;                      // plane z+1 (3D)
+    int32_t* s_mp = smem + 2 * PL;                              // when HASMP
+    int32_t* s_lo = smem + (HASMP ? 2 : 1) * 2 * PL;            // plane z-1 (3D)
+    int32_t* s_hi = s_lo + 2 * PL;                              // plane z+1 (3D)
+    uint32_t* queue = reinterpret_cast<uint32_t*>(smem + 2 * PL * Cfg::planes + (HASMP ? 2 * PL : 0));
+    int* qn = reinterpret_cast<int*>(queue + Cfg::QCAP);
 
     const int tile = blockIdx.x;
     const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
@@ -216,98 +279,115 @@ __global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
     const int z = Z ? 2 * (int)blockIdx.y + a.zpar : 0;
     const int zlo = Z ? wrapi(z - 1, a.Lz) : 0, zhi = Z ? wrapi(z + 1, a.Lz) : 0;
     const int64_t sxy = (int64_t)a.Lx * a.Ly;
-    const int32_t* qp = a.q_in + sxy * z;
-    const int32_t* mpp = HASMP ? a.mp_in + sxy * z : nullptr;
 
-    for (int idx = threadIdx.x; idx < WN; idx += kThreads) {
-        const int ly = idx / WX, lx = idx - ly * WX;
-        const int gx = wrapi(x0 - H + lx, a.Lx), gy = wrapi(y0 - H + ly, a.Ly);
-        const int64_t o = gx + (int64_t)a.Lx * gy;
-        s_q[idx] = qp[o];
-        if (HASMP) s_mp[idx] = mpp[o];
-        if (Z) {
-            s_lo[idx] = a.q_nb[sxy * zlo + o];
-            s_hi[idx] = a.q_nb[sxy * zhi + o];
-        }
+    if (threadIdx.x < 8) qn[threadIdx.x] = 0;
+    load_window<Cfg>(a, a.q_in + sxy * z, s_q, x0, y0);
+    if (HASMP) load_window<Cfg>(a, a.mp_in + sxy * z, s_mp, x0, y0);
+    if (Z) {
+        load_window<Cfg>(a, a.q_nb + sxy * zlo, s_lo, x0, y0);
+        load_window<Cfg>(a, a.q_nb + sxy * zhi, s_hi, x0, y0);
     }
     __syncthreads();
 
+    const int lane_x = threadIdx.x & (WXH - 1);  // one warp pair per window row
+    const int row_slot = threadIdx.x / WXH;      // kThreads / WXH rows at a time
+    constexpr int ROWS_PER_PASS = kThreads / WXH;
     const int cz = Z ? 4 * a.zpar : 0;
-#pragma unroll 1
+
+#pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int lo = p + 1, hix = WX - p - 1, hiy = WY - p - 1;
-        int nx, ny, xs, ys;
-        if (NBR == 4) {
-            nx = (hix - lo + 1) >> 1;  // sites per row (upper bound)
-            ny = hiy - lo;
-            xs = ys = lo;
-        } else {
-            const int cx = p & 1, cy = p >> 1;
-            xs = lo + ((lo ^ cx) & 1);
-            ys = lo + ((lo ^ cy) & 1);
-            nx = (hix - xs + 1) >> 1;
-            ny = (hiy - ys + 1) >> 1;
-        }
-        const int n = nx * ny;
-        for (int s = threadIdx.x; s < n; s += kThreads) {
-            const int r = s / nx, k = s - r * nx;
-            int lx, ly;
-            if (NBR == 4) {
-                ly = ys + r;
-                lx = xs + ((xs + ly + p) & 1) + 2 * k;
-                if (lx >= hix) continue;
-            } else {
-                lx = xs + 2 * k;
-                ly = ys + 2 * r;
-            }
-            const int li = ly * WX + lx;
-            const int32_t qi = s_q[li];
-            int same_old = 0;
-            if (NBR == 4) {
-                same_old = (s_q[li + 1] == qi) + (s_q[li - 1] == qi) + (s_q[li + WX] == qi) + (s_q[li - WX] == qi);
-            } else {
+        // ---- stage A: interior test, queue the rest --------------------------
+        // rows holding sites of this colour: every row (4-neighbour) or every
+        // other row (Moore, y parity = p >> 1)
+        constexpr int RSTEP = NBR == 4 ? 1 : 2;
+        const int ys = NBR == 4 ? lo : lo + ((lo ^ (p >> 1)) & 1);
+        for (int ly0 = ys; ly0 < hiy; ly0 += RSTEP * ROWS_PER_PASS) {
+            const int ly = ly0 + RSTEP * row_slot;
+            const int px = NBR == 4 ? ((ly + p) & 1) : (p & 1);  // x parity of this colour in row ly
+            const bool rowok = ly < hiy;
+            const int lx = 2 * lane_x + px;
+            bool cand = false;
+            int same = 0;
+            if (rowok && lx >= lo && lx < hix) {
+                const int base = ly * WXH;
+                const int xs = lx >> 1;
+                // same parity column (dx = 0), other parity columns (dx = -1, +1)
+                const int c0 = px * PL + base + xs;
+                const int cl = (px ? 0 : PL) + base + xs - (px ? 0 : 1);
+                const int cr = (px ? 0 : PL) + base + xs + (px ? 1 : 0);
+                const int32_t qi = s_q[c0];
+                if (NBR == 4) {
+                    same = (s_q[cl] == qi) + (s_q[cr] == qi) + (s_q[c0 - WXH] == qi) + (s_q[c0 + WXH] == qi);
+                } else {
 #pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (dx || dy) same_old += s_q[li + dy * WX + dx] == qi;
-                        if (Z) same_old += (s_lo[li + dy * WX + dx] == qi) + (s_hi[li + dy * WX + dx] == qi);
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int o = dy * WXH;
+                        same += (s_q[cl + o] == qi) + (s_q[cr + o] == qi) + (dy ? (s_q[c0 + o] == qi) : 0);
+                        if (Z) {
+                            same += (s_lo[cl + o] == qi) + (s_lo[cr + o] == qi) + (s_lo[c0 + o] == qi);
+                            same += (s_hi[cl + o] == qi) + (s_hi[cr + o] == qi) + (s_hi[c0 + o] == qi);
+                        }
                     }
+                }
+                cand = same != M;
             }
-            if (same_old == M) continue;
-            const int gx = wrapi(x0 - H + lx, a.Lx), gy = wrapi(y0 - H + ly, a.Ly);
+            const unsigned ball = __ballot_sync(0xFFFFFFFFu, cand);
+            if (ball) {
+                const int lane = threadIdx.x & 31;
+                int slot = 0;
+                if (lane == __ffs(ball) - 1) slot = atomicAdd(qn + p, __popc(ball));
+                slot = __shfl_sync(0xFFFFFFFFu, slot, __ffs(ball) - 1);
+                if (cand) {
+                    const int k = slot + __popc(ball & ((1u << lane) - 1));
+                    queue[k] = ((uint32_t)ly << 13) | ((uint32_t)lx << 5) | (uint32_t)same;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- stage B: Metropolis update of the queued sites ----------------
+        const int n = qn[p];
+        for (int k = threadIdx.x; k < n; k += kThreads) {
+            const uint32_t e = queue[k];
+            const int same_old = (int)(e & 31u), lx = (int)((e >> 5) & 255u), ly = (int)(e >> 13);
+            const int px = lx & 1, xs = lx >> 1, base = ly * WXH;
+            const int c0 = px * PL + base + xs;
+            const int cl = (px ? 0 : PL) + base + xs - (px ? 0 : 1);
+            const int cr = (px ? 0 : PL) + base + xs + (px ? 1 : 0);
+            const int32_t qi = s_q[c0];
+            const int gx = a.fast ? wrap1(x0 - H + lx, a.Lx) : wrapi(x0 - H + lx, a.Lx);
+            const int gy = a.fast ? wrap1(y0 - H + ly, a.Ly) : wrapi(y0 - H + ly, a.Ly);
             const int64_t gi = gx + (int64_t)a.Lx * gy + sxy * z;
             const int colour = NBR == 4 ? p : cz + p;
             const uint4 u = draw(a.seed, (uint64_t)gi, a.sweep, kTagSweep, (uint32_t)colour);
             const int kp = (int)__umulhi(u.x, (uint32_t)M);
-            // neighbour kp: plane (-1, 0, +1) and in-plane offset
             int dx, dy, dz;
-            if (NBR == 4) {
-                Geo<2, 4>::off(kp, dx, dy, dz);
-            } else if (NBR == 8) {
-                Geo<2, 8>::off(kp, dx, dy, dz);
-            } else {
-                Geo<3, 26>::off(kp, dx, dy, dz);
-            }
-            const int lj = li + dy * WX + dx;
-            const int32_t qj = dz == 0 ? s_q[lj] : (dz < 0 ? s_lo[lj] : s_hi[lj]);
+            if (NBR == 4) Geo<2, 4>::off(kp, dx, dy, dz);
+            else if (NBR == 8) Geo<2, 8>::off(kp, dx, dy, dz);
+            else Geo<3, 26>::off(kp, dx, dy, dz);
+            const int cj = (dx == 0 ? c0 : (dx < 0 ? cl : cr)) + dy * WXH;
+            const int32_t* pj = dz == 0 ? s_q : (dz < 0 ? s_lo : s_hi);
+            const int32_t qj = pj[cj];
             if (qj == qi) continue;
-            int same_new = 0;
+            int same_new;
             if (NBR == 4) {
-                same_new = (s_q[li + 1] == qj) + (s_q[li - 1] == qj) + (s_q[li + WX] == qj) + (s_q[li - WX] == qj);
+                same_new = (s_q[cl] == qj) + (s_q[cr] == qj) + (s_q[c0 - WXH] == qj) + (s_q[c0 + WXH] == qj);
             } else {
+                same_new = 0;
 #pragma unroll
-                for (int ddy = -1; ddy <= 1; ++ddy)
-#pragma unroll
-                    for (int ddx = -1; ddx <= 1; ++ddx) {
-                        if (ddx || ddy) same_new += s_q[li + ddy * WX + ddx] == qj;
-                        if (Z) same_new += (s_lo[li + ddy * WX + ddx] == qj) + (s_hi[li + ddy * WX + ddx] == qj);
+                for (int ddy = -1; ddy <= 1; ++ddy) {
+                    const int o = ddy * WXH;
+                    same_new += (s_q[cl + o] == qj) + (s_q[cr + o] == qj) + (ddy ? (s_q[c0 + o] == qj) : 0);
+                    if (Z) {
+                        same_new += (s_lo[cl + o] == qj) + (s_lo[cr + o] == qj) + (s_lo[c0 + o] == qj);
+                        same_new += (s_hi[cl + o] == qj) + (s_hi[cr + o] == qj) + (s_hi[c0 + o] == qj);
                     }
+                }
             }
             int32_t mpj = 0;
             if (HASMP) {
                 if (dz == 0) {
-                    mpj = s_mp[lj];
+                    mpj = s_mp[cj];
                 } else {
                     const int jx = wrapi(gx + dx, a.Lx), jy = wrapi(gy + dy, a.Ly);
                     const int jz = dz < 0 ? zlo : zhi;
@@ -316,27 +396,44 @@ __global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
             }
             int32_t db = 0;
             if (FIELD == 1) db = tab(a.table, a.table_n, qj) - tab(a.table, a.table_n, qi);
-            if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, s_mp[li]);
+            if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, s_mp[c0]);
             const int32_t d = a.J * (same_old - same_new) + db;
             if (metropolis(d, a.D, a.thr, u.y)) {
-                s_q[li] = qj;
-                if (HASMP) s_mp[li] = mpj;
+                s_q[c0] = qj;
+                if (HASMP) s_mp[c0] = mpj;
             }
         }
         __syncthreads();
     }
 
-    // write the core of the tile (skip the part of a ragged tile beyond the lattice)
+    // ---- write the tile's core (skip columns/rows beyond a ragged edge) -----
     int32_t* qo = a.q_out + sxy * z;
     int32_t* mpo = HASMP ? a.mp_out + sxy * z : nullptr;
-    for (int idx = threadIdx.x; idx < TX * TY; idx += kThreads) {
-        const int cy = idx / TX, cx = idx - cy * TX;
-        const int gx = x0 + cx, gy = y0 + cy;
-        if (gx >= a.Lx || gy >= a.Ly) continue;
-        const int li = (cy + H) * WX + cx + H;
-        const int64_t o = gx + (int64_t)a.Lx * gy;
-        qo[o] = s_q[li];
-        if (HASMP) mpo[o] = s_mp[li];
+    if (a.vec) {
+        constexpr int CH = TX / 4;
+        for (int idx = threadIdx.x; idx < CH * TY; idx += kThreads) {
+            const int cy = idx / CH, c = idx - cy * CH;
+            const int gx = x0 + 4 * c, gy = y0 + cy;
+            if (gx >= a.Lx || gy >= a.Ly) continue;
+            const int r = (cy + H) * WXH + ((H + 4 * c) >> 1);
+            const int2 ev = *reinterpret_cast<const int2*>(s_q + r), od = *reinterpret_cast<const int2*>(s_q + PL + r);
+            *reinterpret_cast<int4*>(qo + gx + (int64_t)a.Lx * gy) = make_int4(ev.x, od.x, ev.y, od.y);
+            if (HASMP) {
+                const int2 me = *reinterpret_cast<const int2*>(s_mp + r), mo = *reinterpret_cast<const int2*>(s_mp + PL + r);
+                *reinterpret_cast<int4*>(mpo + gx + (int64_t)a.Lx * gy) = make_int4(me.x, mo.x, me.y, mo.y);
+            }
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < TX * TY; idx += kThreads) {
+            const int cy = idx / TX, cx = idx - cy * TX;
+            const int gx = x0 + cx, gy = y0 + cy;
+            if (gx >= a.Lx || gy >= a.Ly) continue;
+            const int lx = cx + H, ly = cy + H;
+            const int li = (lx & 1) * PL + ly * WXH + (lx >> 1);
+            const int64_t o = gx + (int64_t)a.Lx * gy;
+            qo[o] = s_q[li];
+            if (HASMP) mpo[o] = s_mp[li];
+        }
     }
 }
 
@@ -389,18 +486,16 @@ int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
 }
 
 template <int NBR>
-struct PlaneTile {
-    static constexpr int TX = 64, TY = NBR == 26 ? 32 : 64;
+struct PlaneTY {
+    static constexpr int TY = NBR == 26 ? 32 : 64;
 };
 
 template <int NBR, int FIELD, bool HASMP>
 int launch_plane(const PlaneArgs& a, int tiles, int planes, cudaStream_t s) {
-    constexpr int TX = PlaneTile<NBR>::TX, TY = PlaneTile<NBR>::TY;
-    constexpr int H = NBR == 4 ? 2 : 4;
-    constexpr int WN = (TX + 2 * H) * (TY + 2 * H);
-    constexpr int arrays = 1 + (HASMP ? 1 : 0) + (NBR == 26 ? 2 : 0);
-    const size_t smem = sizeof(int32_t) * WN * arrays;
-    auto fn = k_plane<NBR, TX, TY, FIELD, HASMP>;
+    constexpr int TY = PlaneTY<NBR>::TY;
+    using Cfg = PlaneCfg<NBR, TY>;
+    const size_t smem = Cfg::smem(HASMP);
+    auto fn = k_plane<NBR, TY, FIELD, HASMP>;
     static bool configured = false;  // per template instance
     if (!configured) {
         HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -447,11 +542,12 @@ int run_plane_kernel(hp_handle* h, const int32_t* q_in, const int32_t* mp_in, co
     a.Lz = (int)h->lat.L[2];
     a.zpar = zpar;
     const int nbr = h->lat.nbr;
-    int TX, TY;
-    if (nbr == 4) { TX = PlaneTile<4>::TX; TY = PlaneTile<4>::TY; }
-    else if (nbr == 8) { TX = PlaneTile<8>::TX; TY = PlaneTile<8>::TY; }
-    else { TX = PlaneTile<26>::TX; TY = PlaneTile<26>::TY; }
+    const int TX = PlaneCfg<8, 64>::TX;
+    const int TY = nbr == 26 ? PlaneTY<26>::TY : PlaneTY<8>::TY;
+    const int WY = TY + 2 * PlaneCfg<8, 64>::H;
     a.tiles_x = (a.Lx + TX - 1) / TX;
+    a.fast = (a.Lx >= PlaneCfg<8, 64>::WX && a.Ly >= WY) ? 1 : 0;
+    a.vec = (a.fast && (a.Lx % 4) == 0) ? 1 : 0;
     const int tiles = a.tiles_x * ((a.Ly + TY - 1) / TY);
     const int planes = nbr == 26 ? a.Lz / 2 : 1;
     if (nbr == 4) return plane_dispatch<4>(h, a, tiles, planes, s);
