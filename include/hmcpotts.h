@@ -155,6 +155,18 @@ HP_API int hp_set_sweep_kernel(hp_handle* h, int32_t kind);
  * which advances by n_mcs.  On return the state is in the bound buffers.     */
 HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
 
+/* Tile variants of the fused sweep kernel (window width x core height; all
+ * give identical lattices).  hp_sweep_variants: how many exist for `nbr`.
+ * hp_set_sweep_variant: choose one (HP_ERR_ARG if not built for the handle's
+ * field mode).  hp_sweep_autotune: time every variant for n_mcs MCS on a
+ * backup of the bound state (the lattice and sweep counter are restored),
+ * keep the fastest, write per-variant milliseconds to ms_out (host float[n],
+ * -1 for unavailable variants; may be NULL) and the choice to *chosen.
+ * Allocates a temporary copy of the lattice; synchronises `stream`.          */
+HP_API int hp_sweep_variants(int32_t nbr, int32_t* n);
+HP_API int hp_set_sweep_variant(hp_handle* h, int32_t v);
+HP_API int hp_sweep_autotune(hp_handle* h, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream);
+
 HP_API int hp_get_sweep_counter(const hp_handle* h, uint64_t* out);
 HP_API int hp_set_sweep_counter(hp_handle* h, uint64_t value);
 
@@ -186,6 +198,27 @@ HP_API int hp_grain_field(int32_t G, const float* quat, double C11, double C12, 
 /* Philox4x32-10 of n counters (device uint32[4n]) into out (device uint32[4n]),
  * the generator every kernel here draws from (exposed for verification).     */
 HP_API int hp_philox(uint64_t seed, const uint32_t* ctr, int64_t n, uint32_t* out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Ensembles: many independent lattices of uneven size, temperature, load and  */
+/* seed swept together (the paper averages 10-100 independent runs, Sec. 4-5). */
+/* ------------------------------------------------------------------------ */
+typedef struct hp_ensemble hp_ensemble;
+
+/* Group R handles (borrowed; each already bound, with its threshold table and
+ * field set) that share dim, nbr, field mode and whether mp is bound.  Every
+ * member keeps its own seed, sweep counter, temperature (threshold table) and
+ * field.                                                                       */
+HP_API int hp_ensemble_create(hp_handle* const* members, int32_t R, hp_ensemble** out);
+HP_API int hp_ensemble_destroy(hp_ensemble* e);
+HP_API int hp_ensemble_set_variant(hp_ensemble* e, int32_t v);
+/* Pick the fastest tile variant for the whole ensemble (state restored).      */
+HP_API int hp_ensemble_autotune(hp_ensemble* e, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream);
+/* Sweep every member n_mcs MCS, bit-identical to hp_sweep on each member.  All
+ * replicas share each launch (one CTA per replica tile); the n_mcs launches are
+ * captured once into a CUDA graph (re-captured when n_mcs or the variant
+ * changes) and replayed as one graph launch on `stream`.                      */
+HP_API int hp_ensemble_sweep(hp_ensemble* e, int32_t n_mcs, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Monte Carlo crystal plasticity (Sec. 2, Eqs. (1)-(3), Table 1) and the     */

@@ -15,6 +15,7 @@ static thread_local std::string g_last_error;
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch_n(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int set_error(int code, const std::string& msg) {
     g_last_error = msg;

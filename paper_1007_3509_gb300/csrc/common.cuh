@@ -32,8 +32,10 @@ int cuda_error(cudaError_t e, const char* what);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// Process-wide count of kernel launches issued by this library.
+// Process-wide count of kernel launches issued by this library (graph
+// replays add their kernel nodes).
 void count_launch();
+void count_launch_n(unsigned long long n);
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11).  Counter words: unit lo, unit hi,
@@ -85,6 +87,7 @@ struct hp_handle {
     int32_t thr_cap = 0;
     uint64_t sweep = 0;
     int sweep_kernel = HP_SWEEP_AUTO;
+    int sweep_variant = 0;      // tile variant of the fused kernel (autotuned)
 };
 
 namespace hp {

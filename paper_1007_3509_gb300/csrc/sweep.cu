@@ -207,6 +207,7 @@ struct PlaneArgs {
     int Lx, Ly, Lz;
     int zpar;               // 3D: parity of the planes handled by this launch
     int tiles_x;
+    int tiles;              // tiles per plane
     int fast;               // 1: window narrower than the lattice (wrap by one add)
     int vec;                // 1: fast and Lx % 4 == 0 (16-byte row chunks)
 };
@@ -216,10 +217,11 @@ __device__ __forceinline__ int wrap1(int a, int L) {
     return a - (a >= L ? L : 0);
 }
 
-template <int NBR, int TY>
+template <int NBR, int WX_, int TY>
 struct PlaneCfg {
     static constexpr int H = 4;
-    static constexpr int WX = 128, WXH = 64, TX = WX - 2 * H;
+    static constexpr int WX = WX_, WXH = WX_ / 2, TX = WX - 2 * H;
+    static_assert(WX == 64 || WX == 128, "window width");
     static constexpr int WY = TY + 2 * H;
     static constexpr int PL = WY * WXH;                  // one parity half of a window plane
     static constexpr int NP = NBR == 4 ? 2 : 4;          // colour phases in a plane
@@ -258,14 +260,13 @@ __device__ __forceinline__ void load_window(const PlaneArgs& a, const int32_t* _
     }
 }
 
-template <int NBR, int TY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
-    using Cfg = PlaneCfg<NBR, TY>;
+template <int NBR, int WX_, int TY, int FIELD, bool HASMP>
+__device__ __forceinline__ void plane_body(const PlaneArgs& a, const int tile, const int zidx, int32_t* smem) {
+    using Cfg = PlaneCfg<NBR, WX_, TY>;
     constexpr int H = Cfg::H, WX = Cfg::WX, WXH = Cfg::WXH, WY = Cfg::WY, PL = Cfg::PL, TX = Cfg::TX;
     constexpr int NP = Cfg::NP;
     constexpr bool Z = Cfg::Z;
     constexpr int M = NBR;
-    extern __shared__ __align__(16) int32_t smem[];
     int32_t* s_q = smem;
     int32_t* s_mp = smem + 2 * PL;                              // when HASMP
     int32_t* s_lo = smem + (HASMP ? 2 : 1) * 2 * PL;            // plane z-1 (3D)
@@ -273,10 +274,9 @@ __global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
     uint32_t* queue = reinterpret_cast<uint32_t*>(smem + 2 * PL * Cfg::planes + (HASMP ? 2 * PL : 0));
     int* qn = reinterpret_cast<int*>(queue + Cfg::QCAP);
 
-    const int tile = blockIdx.x;
     const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
     const int x0 = tx * TX, y0 = ty * TY;
-    const int z = Z ? 2 * (int)blockIdx.y + a.zpar : 0;
+    const int z = Z ? 2 * zidx + a.zpar : 0;
     const int zlo = Z ? wrapi(z - 1, a.Lz) : 0, zhi = Z ? wrapi(z + 1, a.Lz) : 0;
     const int64_t sxy = (int64_t)a.Lx * a.Ly;
 
@@ -437,6 +437,45 @@ __global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
     }
 }
 
+template <int NBR, int WX, int TY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
+    extern __shared__ __align__(16) int32_t smem[];
+    plane_body<NBR, WX, TY, FIELD, HASMP>(a, (int)blockIdx.x, (int)blockIdx.y, smem);
+}
+
+// Many independent lattices (replicas) in one launch: block b belongs to the
+// replica r with start[r] <= b < start[r+1]; within it, b - start[r] =
+// zidx * tiles + tile.  Each replica carries its own geometry, seed, sweep
+// counter, field table and threshold table in its PlaneArgs.
+struct BatchArgs {
+    const PlaneArgs* args;
+    const int64_t* start;  // R + 1 block offsets
+    int R;
+    uint32_t sweep_add;    // added to every replica's sweep counter
+};
+
+template <int NBR, int WX, int TY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(kThreads) k_plane_batch(BatchArgs b) {
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ PlaneArgs sa;
+    __shared__ int s_tile, s_zidx;
+    if (threadIdx.x == 0) {
+        const int64_t blk = blockIdx.x;
+        int lo = 0, hi = b.R - 1;
+        while (lo < hi) {  // largest r with start[r] <= blk
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.start[mid] <= blk) lo = mid; else hi = mid - 1;
+        }
+        sa = b.args[lo];
+        sa.sweep += b.sweep_add;
+        const int64_t local = blk - b.start[lo];
+        s_zidx = (int)(local / sa.tiles);
+        s_tile = (int)(local - (int64_t)s_zidx * sa.tiles);
+    }
+    __syncthreads();
+    plane_body<NBR, WX, TY, FIELD, HASMP>(sa, s_tile, s_zidx, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------
@@ -485,44 +524,80 @@ int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     return phase_dispatch<3, 26>(h, sweep, colour, s);
 }
 
-template <int NBR>
-struct PlaneTY {
-    static constexpr int TY = NBR == 26 ? 32 : 64;
+// Tile variants of the fused kernel: window width WX (core TX = WX - 8) and
+// core height TY.  All give identical lattices; the autotuner picks one.
+struct Variant {
+    int WX, TY;
 };
+constexpr int kVariants2D = 3, kVariants3D = 4;
+constexpr Variant kV2D[kVariants2D] = {{128, 64}, {128, 32}, {64, 64}};
+constexpr Variant kV3D[kVariants3D] = {{128, 32}, {128, 16}, {64, 32}, {64, 16}};
 
-template <int NBR, int FIELD, bool HASMP>
-int launch_plane(const PlaneArgs& a, int tiles, int planes, cudaStream_t s) {
-    constexpr int TY = PlaneTY<NBR>::TY;
-    using Cfg = PlaneCfg<NBR, TY>;
+int n_variants(int nbr) { return nbr == 26 ? kVariants3D : (nbr == 6 ? 1 : kVariants2D); }
+Variant variant_of(int nbr, int v) { return nbr == 26 ? kV3D[v] : kV2D[v]; }
+
+template <int NBR, int WX, int TY, int FIELD, bool HASMP>
+int launch_one(const PlaneArgs* a, const BatchArgs* b, int64_t blocks, int planes, cudaStream_t s) {
+    using Cfg = PlaneCfg<NBR, WX, TY>;
     const size_t smem = Cfg::smem(HASMP);
-    auto fn = k_plane<NBR, TY, FIELD, HASMP>;
     static bool configured = false;  // per template instance
     if (!configured) {
-        HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HP_CUDA(cudaFuncSetAttribute(k_plane<NBR, WX, TY, FIELD, HASMP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HP_CUDA(cudaFuncSetAttribute(k_plane_batch<NBR, WX, TY, FIELD, HASMP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
+    if (blocks == 0) return HP_OK;  // configure only
     ::hp::count_launch();
-    fn<<<dim3((unsigned)tiles, (unsigned)planes), kThreads, smem, s>>>(a);
+    if (a) k_plane<NBR, WX, TY, FIELD, HASMP><<<dim3((unsigned)blocks, (unsigned)planes), kThreads, smem, s>>>(*a);
+    else k_plane_batch<NBR, WX, TY, FIELD, HASMP><<<(unsigned)blocks, kThreads, smem, s>>>(*b);
     HP_LAUNCH_CHECK("k_plane");
     return HP_OK;
 }
 
-template <int NBR>
-int plane_dispatch(hp_handle* h, const PlaneArgs& a, int tiles, int planes, cudaStream_t s) {
-    const bool m = h->mp != nullptr;
-    switch (h->desc.field_mode) {
-        case HP_FIELD_NONE:
-            return m ? launch_plane<NBR, 0, true>(a, tiles, planes, s) : launch_plane<NBR, 0, false>(a, tiles, planes, s);
-        case HP_FIELD_GRAIN:
-            return m ? launch_plane<NBR, 1, true>(a, tiles, planes, s) : launch_plane<NBR, 1, false>(a, tiles, planes, s);
-        default:
-            return launch_plane<NBR, 2, true>(a, tiles, planes, s);
+// field / material-point combinations; variants other than 0 are compiled for
+// the two production combinations only (grain field without mp, point field)
+template <int NBR, int WX, int TY, bool ALL>
+int launch_fm(int field, bool m, const PlaneArgs* a, const BatchArgs* b, int64_t blocks, int planes,
+              cudaStream_t s) {
+    if (field == HP_FIELD_GRAIN && !m) return launch_one<NBR, WX, TY, 1, false>(a, b, blocks, planes, s);
+    if (field == HP_FIELD_POINT) return launch_one<NBR, WX, TY, 2, true>(a, b, blocks, planes, s);
+    if constexpr (ALL) {
+        if (field == HP_FIELD_NONE) return m ? launch_one<NBR, WX, TY, 0, true>(a, b, blocks, planes, s)
+                                             : launch_one<NBR, WX, TY, 0, false>(a, b, blocks, planes, s);
+        return launch_one<NBR, WX, TY, 1, true>(a, b, blocks, planes, s);
     }
+    return set_error(HP_ERR_ARG, "sweep: tile variant not built for this field mode");
 }
 
-int run_plane_kernel(hp_handle* h, const int32_t* q_in, const int32_t* mp_in, const int32_t* q_nb,
-                     const int32_t* mp_nb, int32_t* q_out, int32_t* mp_out, uint32_t sweep, int zpar,
-                     cudaStream_t s) {
+int launch_variant(int nbr, int v, int field, bool m, const PlaneArgs* a, const BatchArgs* b, int64_t blocks,
+                   int planes, cudaStream_t s) {
+    if (nbr == 4) {
+        if (v == 0) return launch_fm<4, 128, 64, true>(field, m, a, b, blocks, planes, s);
+        if (v == 1) return launch_fm<4, 128, 32, false>(field, m, a, b, blocks, planes, s);
+        return launch_fm<4, 64, 64, false>(field, m, a, b, blocks, planes, s);
+    }
+    if (nbr == 8) {
+        if (v == 0) return launch_fm<8, 128, 64, true>(field, m, a, b, blocks, planes, s);
+        if (v == 1) return launch_fm<8, 128, 32, false>(field, m, a, b, blocks, planes, s);
+        return launch_fm<8, 64, 64, false>(field, m, a, b, blocks, planes, s);
+    }
+    if (v == 0) return launch_fm<26, 128, 32, true>(field, m, a, b, blocks, planes, s);
+    if (v == 1) return launch_fm<26, 128, 16, false>(field, m, a, b, blocks, planes, s);
+    if (v == 2) return launch_fm<26, 64, 32, false>(field, m, a, b, blocks, planes, s);
+    return launch_fm<26, 64, 16, false>(field, m, a, b, blocks, planes, s);
+}
+
+bool variant_ok(int nbr, int v, int field, bool m) {
+    if (v < 0 || v >= n_variants(nbr)) return false;
+    return v == 0 || (field == HP_FIELD_GRAIN && !m) || field == HP_FIELD_POINT;
+}
+
+// Arguments of the fused kernel for one lattice and one launch.
+PlaneArgs plane_args(const hp_handle* h, int variant, const int32_t* q_in, const int32_t* mp_in,
+                     const int32_t* q_nb, const int32_t* mp_nb, int32_t* q_out, int32_t* mp_out, uint32_t sweep,
+                     int zpar, int* planes) {
     PlaneArgs a;
     a.q_in = q_in;
     a.mp_in = mp_in;
@@ -541,19 +616,32 @@ int run_plane_kernel(hp_handle* h, const int32_t* q_in, const int32_t* mp_in, co
     a.Ly = (int)h->lat.L[1];
     a.Lz = (int)h->lat.L[2];
     a.zpar = zpar;
-    const int nbr = h->lat.nbr;
-    const int TX = PlaneCfg<8, 64>::TX;
-    const int TY = nbr == 26 ? PlaneTY<26>::TY : PlaneTY<8>::TY;
-    const int WY = TY + 2 * PlaneCfg<8, 64>::H;
+    const Variant v = variant_of(h->lat.nbr, variant);
+    const int TX = v.WX - 8, WY = v.TY + 8;
     a.tiles_x = (a.Lx + TX - 1) / TX;
-    a.fast = (a.Lx >= PlaneCfg<8, 64>::WX && a.Ly >= WY) ? 1 : 0;
+    a.tiles = a.tiles_x * ((a.Ly + v.TY - 1) / v.TY);
+    a.fast = (a.Lx >= v.WX && a.Ly >= WY) ? 1 : 0;
     a.vec = (a.fast && (a.Lx % 4) == 0) ? 1 : 0;
-    const int tiles = a.tiles_x * ((a.Ly + TY - 1) / TY);
-    const int planes = nbr == 26 ? a.Lz / 2 : 1;
-    if (nbr == 4) return plane_dispatch<4>(h, a, tiles, planes, s);
-    if (nbr == 8) return plane_dispatch<8>(h, a, tiles, planes, s);
-    return plane_dispatch<26>(h, a, tiles, planes, s);
+    *planes = h->lat.nbr == 26 ? a.Lz / 2 : 1;
+    return a;
 }
+
+int plane_launch(const hp_handle* h, int variant, const PlaneArgs& a, int planes, cudaStream_t s) {
+    return launch_variant(h->lat.nbr, variant, h->desc.field_mode, h->mp != nullptr, &a, nullptr, a.tiles, planes, s);
+}
+
+int plane_launch_batch(int nbr, int variant, int field, bool m, const PlaneArgs* d_args, const int64_t* d_start,
+                       int R, int64_t blocks, uint32_t sweep_add, cudaStream_t s) {
+    BatchArgs b;
+    b.args = d_args;
+    b.start = d_start;
+    b.R = R;
+    b.sweep_add = sweep_add;
+    return launch_variant(nbr, variant, field, m, nullptr, &b, blocks, 1, s);
+}
+
+int sweep_variants(int nbr) { return n_variants(nbr); }
+bool sweep_variant_ok(int nbr, int v, int field, bool m) { return variant_ok(nbr, v, field, m); }
 
 }  // namespace
 
@@ -571,16 +659,20 @@ int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
         return HP_OK;
     }
     const bool m = h->mp != nullptr;
+    const int v = h->sweep_variant;
     int32_t *qc = h->q, *mc = h->mp, *qa = h->q_alt, *ma = m ? h->mp_alt : nullptr;
     for (int32_t t = 0; t < n_mcs; ++t) {
         const uint32_t sw = (uint32_t)(h->sweep + t);
-        int rc;
+        int planes = 1, rc;
         if (nbr == 26) {
-            rc = run_plane_kernel(h, qc, mc, qc, mc, qa, ma, sw, 0, s);
+            const PlaneArgs a0 = plane_args(h, v, qc, mc, qc, mc, qa, ma, sw, 0, &planes);
+            rc = plane_launch(h, v, a0, planes, s);
             if (rc) return rc;
-            rc = run_plane_kernel(h, qc, mc, qa, ma, qa, ma, sw, 1, s);
+            const PlaneArgs a1 = plane_args(h, v, qc, mc, qa, ma, qa, ma, sw, 1, &planes);
+            rc = plane_launch(h, v, a1, planes, s);
         } else {
-            rc = run_plane_kernel(h, qc, mc, nullptr, nullptr, qa, ma, sw, 0, s);
+            const PlaneArgs a0 = plane_args(h, v, qc, mc, nullptr, nullptr, qa, ma, sw, 0, &planes);
+            rc = plane_launch(h, v, a0, planes, s);
         }
         if (rc) return rc;
         int32_t* tq = qc; qc = qa; qa = tq;
@@ -596,3 +688,287 @@ int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
 }
 
 }  // namespace hp
+
+// ---------------------------------------------------------------------------
+// Autotuner and batched ensembles (C ABI)
+// ---------------------------------------------------------------------------
+#include <vector>
+
+using namespace hp;
+
+extern "C" int hp_sweep_autotune(hp_handle* h, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream) {
+    if (!h || n_mcs < 1) return set_error(HP_ERR_ARG, "hp_sweep_autotune: bad arguments");
+    if (!h->q || !h->thr) return set_error(HP_ERR_STATE, "hp_sweep_autotune: bind buffers and thresholds first");
+    cudaStream_t s = as_stream(stream);
+    const int nbr = h->lat.nbr;
+    const int nv = sweep_variants(nbr);
+    const bool m = h->mp != nullptr;
+    const size_t bytes = sizeof(int32_t) * (size_t)h->lat.N;
+    int32_t *bq = nullptr, *bm = nullptr;
+    HP_CUDA(cudaMallocAsync((void**)&bq, bytes, s));
+    if (m && cudaMallocAsync((void**)&bm, bytes, s) != cudaSuccess) {
+        cudaFreeAsync(bq, s);
+        return set_error(HP_ERR_OOM, "hp_sweep_autotune: backup allocation failed");
+    }
+    cudaMemcpyAsync(bq, h->q, bytes, cudaMemcpyDeviceToDevice, s);
+    if (m) cudaMemcpyAsync(bm, h->mp, bytes, cudaMemcpyDeviceToDevice, s);
+    const uint64_t sweep0 = h->sweep;
+    const int kernel0 = h->sweep_kernel;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0, rc = HP_OK;
+    float best_ms = 3.4e38f;
+    h->sweep_kernel = HP_SWEEP_FUSED;
+    for (int v = 0; v < nv && rc == HP_OK; ++v) {
+        if (ms_out) ms_out[v] = -1.0f;
+        if (!sweep_variant_ok(nbr, v, h->desc.field_mode, m)) continue;
+        h->sweep_variant = v;
+        h->sweep = sweep0;
+        rc = sweep_run(h, 1, s);  // warm-up (also configures the kernel)
+        if (rc) break;
+        cudaMemcpyAsync(h->q, bq, bytes, cudaMemcpyDeviceToDevice, s);
+        if (m) cudaMemcpyAsync(h->mp, bm, bytes, cudaMemcpyDeviceToDevice, s);
+        h->sweep = sweep0;
+        cudaEventRecord(e0, s);
+        rc = sweep_run(h, n_mcs, s);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_error(cudaGetLastError(), "hp_sweep_autotune"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+        cudaMemcpyAsync(h->q, bq, bytes, cudaMemcpyDeviceToDevice, s);
+        if (m) cudaMemcpyAsync(h->mp, bm, bytes, cudaMemcpyDeviceToDevice, s);
+    }
+    h->sweep = sweep0;
+    h->sweep_kernel = kernel0;
+    h->sweep_variant = best;
+    cudaFreeAsync(bq, s);
+    if (bm) cudaFreeAsync(bm, s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == HP_OK) rc = cuda_error(cudaGetLastError(), "hp_sweep_autotune");
+    if (chosen) *chosen = best;
+    return rc;
+}
+
+struct hp_ensemble {
+    std::vector<hp_handle*> m;
+    int nbr = 0, field = 0;
+    bool hasmp = false;
+    int variant = 0;
+    std::vector<PlaneArgs> args;   // [mcs parity][zpar][R]
+    std::vector<int64_t> start;    // R + 1
+    PlaneArgs* d_args = nullptr;
+    int64_t* d_start = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int exec_n = -1, exec_variant = -1;
+    unsigned long long exec_kernels = 0;
+};
+
+namespace {
+
+int ensemble_build(hp_ensemble* e, cudaStream_t s) {
+    const int R = (int)e->m.size();
+    e->args.assign((size_t)4 * R, PlaneArgs{});
+    e->start.assign((size_t)R + 1, 0);
+    for (int r = 0; r < R; ++r) {
+        hp_handle* h = e->m[r];
+        int planes = 1;
+        for (int k = 0; k < 2; ++k) {
+            int32_t* in_q = k == 0 ? h->q : h->q_alt;
+            int32_t* out_q = k == 0 ? h->q_alt : h->q;
+            int32_t* in_m = e->hasmp ? (k == 0 ? h->mp : h->mp_alt) : nullptr;
+            int32_t* out_m = e->hasmp ? (k == 0 ? h->mp_alt : h->mp) : nullptr;
+            e->args[(size_t)(2 * k + 0) * R + r] =
+                plane_args(h, e->variant, in_q, in_m, in_q, in_m, out_q, out_m, (uint32_t)h->sweep, 0, &planes);
+            e->args[(size_t)(2 * k + 1) * R + r] =
+                plane_args(h, e->variant, in_q, in_m, out_q, out_m, out_q, out_m, (uint32_t)h->sweep, 1, &planes);
+        }
+        e->start[r + 1] = e->start[r] + (int64_t)e->args[r].tiles * planes;
+    }
+    HP_CUDA(cudaMemcpyAsync(e->d_args, e->args.data(), sizeof(PlaneArgs) * e->args.size(), cudaMemcpyHostToDevice, s));
+    HP_CUDA(cudaMemcpyAsync(e->d_start, e->start.data(), sizeof(int64_t) * e->start.size(), cudaMemcpyHostToDevice, s));
+    return HP_OK;
+}
+
+int ensemble_launches(hp_ensemble* e, int32_t n, cudaStream_t s, unsigned long long* kernels) {
+    const int R = (int)e->m.size();
+    const int64_t blocks = e->start[R];
+    unsigned long long nk = 0;
+    for (int32_t t = 0; t < n; ++t) {
+        const int k = t & 1;
+        for (int zp = 0; zp < (e->nbr == 26 ? 2 : 1); ++zp) {
+            const int rc = plane_launch_batch(e->nbr, e->variant, e->field, e->hasmp, e->d_args + (size_t)(2 * k + zp) * R,
+                                              e->d_start, R, blocks, (uint32_t)t, s);
+            if (rc) return rc;
+            ++nk;
+        }
+    }
+    if (n & 1)
+        for (hp_handle* h : e->m) {
+            const size_t bytes = sizeof(int32_t) * (size_t)h->lat.N;
+            HP_CUDA(cudaMemcpyAsync(h->q, h->q_alt, bytes, cudaMemcpyDeviceToDevice, s));
+            if (e->hasmp) HP_CUDA(cudaMemcpyAsync(h->mp, h->mp_alt, bytes, cudaMemcpyDeviceToDevice, s));
+        }
+    if (kernels) *kernels = nk;
+    return HP_OK;
+}
+
+}  // namespace
+
+extern "C" int hp_ensemble_create(hp_handle* const* members, int32_t R, hp_ensemble** out) {
+    if (!members || R < 1 || !out) return set_error(HP_ERR_ARG, "hp_ensemble_create: bad arguments");
+    *out = nullptr;
+    const hp_handle* h0 = members[0];
+    if (!h0) return set_error(HP_ERR_ARG, "hp_ensemble_create: null member");
+    for (int r = 0; r < R; ++r) {
+        const hp_handle* h = members[r];
+        if (!h) return set_error(HP_ERR_ARG, "hp_ensemble_create: null member");
+        if (h->lat.nbr != h0->lat.nbr || h->lat.dim != h0->lat.dim || h->desc.field_mode != h0->desc.field_mode ||
+            (h->mp != nullptr) != (h0->mp != nullptr))
+            return set_error(HP_ERR_ARG, "hp_ensemble_create: members must share dim, nbr, field mode and mp binding");
+        if (!h->q || !h->thr || (h->desc.field_mode != HP_FIELD_NONE && !h->table))
+            return set_error(HP_ERR_STATE, "hp_ensemble_create: every member needs buffers, thresholds and field");
+    }
+    if (h0->lat.nbr == 6) return set_error(HP_ERR_ARG, "hp_ensemble_create: no fused kernel for 3D 6-neighbour lattices");
+    hp_ensemble* e = new (std::nothrow) hp_ensemble();
+    if (!e) return set_error(HP_ERR_OOM, "hp_ensemble_create: out of host memory");
+    e->m.assign(members, members + R);
+    e->nbr = h0->lat.nbr;
+    e->field = h0->desc.field_mode;
+    e->hasmp = h0->mp != nullptr;
+    if (cudaMalloc((void**)&e->d_args, sizeof(PlaneArgs) * 4 * (size_t)R) != cudaSuccess ||
+        cudaMalloc((void**)&e->d_start, sizeof(int64_t) * ((size_t)R + 1)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(e->d_args);
+        cudaFree(e->d_start);
+        delete e;
+        return set_error(HP_ERR_OOM, "hp_ensemble_create: device allocation failed");
+    }
+    *out = e;
+    return HP_OK;
+}
+
+extern "C" int hp_ensemble_destroy(hp_ensemble* e) {
+    if (!e) return HP_OK;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    cudaFree(e->d_args);
+    cudaFree(e->d_start);
+    delete e;
+    return HP_OK;
+}
+
+extern "C" int hp_set_sweep_variant(hp_handle* h, int32_t v) {
+    if (!h || !sweep_variant_ok(h->lat.nbr, v, h->desc.field_mode, h->mp != nullptr))
+        return set_error(HP_ERR_ARG, "hp_set_sweep_variant: variant not available for this lattice");
+    h->sweep_variant = v;
+    return HP_OK;
+}
+
+extern "C" int hp_sweep_variants(int32_t nbr, int32_t* n) {
+    if (!n) return set_error(HP_ERR_ARG, "hp_sweep_variants: null argument");
+    *n = sweep_variants(nbr);
+    return HP_OK;
+}
+
+extern "C" int hp_ensemble_set_variant(hp_ensemble* e, int32_t v) {
+    if (!e || !sweep_variant_ok(e->nbr, v, e->field, e->hasmp))
+        return set_error(HP_ERR_ARG, "hp_ensemble_set_variant: variant not available");
+    e->variant = v;
+    return HP_OK;
+}
+
+extern "C" int hp_ensemble_sweep(hp_ensemble* e, int32_t n_mcs, void* stream) {
+    if (!e || n_mcs < 0) return set_error(HP_ERR_ARG, "hp_ensemble_sweep: bad arguments");
+    if (n_mcs == 0) return HP_OK;
+    cudaStream_t s = as_stream(stream);
+    int rc = ensemble_build(e, s);  // refresh per-member sweep counters
+    if (rc) return rc;
+    if (!e->exec || e->exec_n != n_mcs || e->exec_variant != e->variant) {
+        if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
+        // kernel attributes are set outside the capture
+        rc = plane_launch_batch(e->nbr, e->variant, e->field, e->hasmp, e->d_args, e->d_start, 1, 0, 0, s);
+        if (rc) return rc;
+        cudaGraph_t g = nullptr;
+        HP_CUDA(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
+        unsigned long long nk = 0;
+        rc = ensemble_launches(e, n_mcs, e->cap, &nk);
+        const cudaError_t ce = cudaStreamEndCapture(e->cap, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (ce != cudaSuccess) return cuda_error(ce, "hp_ensemble_sweep: capture");
+        const cudaError_t ie = cudaGraphInstantiate(&e->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) { e->exec = nullptr; return cuda_error(ie, "hp_ensemble_sweep: instantiate"); }
+        e->exec_n = n_mcs;
+        e->exec_variant = e->variant;
+        e->exec_kernels = nk;
+    } else {
+        count_launch_n(e->exec_kernels);
+    }
+    HP_CUDA(cudaGraphLaunch(e->exec, s));
+    for (hp_handle* h : e->m) h->sweep += (uint64_t)n_mcs;
+    return HP_OK;
+}
+
+extern "C" int hp_ensemble_autotune(hp_ensemble* e, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream) {
+    if (!e || n_mcs < 1) return set_error(HP_ERR_ARG, "hp_ensemble_autotune: bad arguments");
+    cudaStream_t s = as_stream(stream);
+    // back up every member's state, time each variant with direct launches, restore
+    std::vector<int32_t*> bq(e->m.size(), nullptr), bm(e->m.size(), nullptr);
+    int rc = HP_OK;
+    for (size_t r = 0; r < e->m.size() && rc == HP_OK; ++r) {
+        const size_t bytes = sizeof(int32_t) * (size_t)e->m[r]->lat.N;
+        if (cudaMallocAsync((void**)&bq[r], bytes, s) != cudaSuccess ||
+            (e->hasmp && cudaMallocAsync((void**)&bm[r], bytes, s) != cudaSuccess))
+            rc = set_error(HP_ERR_OOM, "hp_ensemble_autotune: backup allocation failed");
+        else {
+            cudaMemcpyAsync(bq[r], e->m[r]->q, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e->hasmp) cudaMemcpyAsync(bm[r], e->m[r]->mp, bytes, cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    auto restore = [&]() {
+        for (size_t r = 0; r < e->m.size(); ++r) {
+            const size_t bytes = sizeof(int32_t) * (size_t)e->m[r]->lat.N;
+            cudaMemcpyAsync(e->m[r]->q, bq[r], bytes, cudaMemcpyDeviceToDevice, s);
+            if (e->hasmp) cudaMemcpyAsync(e->m[r]->mp, bm[r], bytes, cudaMemcpyDeviceToDevice, s);
+        }
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 3.4e38f;
+    const int v0 = e->variant;
+    for (int v = 0; v < sweep_variants(e->nbr) && rc == HP_OK; ++v) {
+        if (ms_out) ms_out[v] = -1.0f;
+        if (!sweep_variant_ok(e->nbr, v, e->field, e->hasmp)) continue;
+        e->variant = v;
+        if ((rc = ensemble_build(e, s))) break;
+        if ((rc = ensemble_launches(e, 1, s, nullptr))) break;  // warm-up
+        restore();
+        cudaEventRecord(e0, s);
+        if ((rc = ensemble_launches(e, n_mcs, s, nullptr))) break;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_error(cudaGetLastError(), "hp_ensemble_autotune"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) ms_out[v] = ms;
+        if (ms < best_ms) { best_ms = ms; best = v; }
+        restore();
+    }
+    e->variant = rc == HP_OK ? best : v0;
+    for (size_t r = 0; r < e->m.size(); ++r) {
+        if (bq[r]) cudaFreeAsync(bq[r], s);
+        if (bm[r]) cudaFreeAsync(bm[r], s);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == HP_OK) rc = cuda_error(cudaGetLastError(), "hp_ensemble_autotune");
+    if (chosen) *chosen = e->variant;
+    return rc;
+}

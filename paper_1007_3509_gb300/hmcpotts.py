@@ -61,6 +61,14 @@ _SIGS = {
     "hp_set_threshold_table": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "hp_set_sweep_kernel": ([C.c_void_p, C.c_int32], C.c_int),
     "hp_sweep": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "hp_sweep_variants": ([C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "hp_set_sweep_variant": ([C.c_void_p, C.c_int32], C.c_int),
+    "hp_sweep_autotune": ([C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p], C.c_int),
+    "hp_ensemble_create": ([C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
+    "hp_ensemble_destroy": ([C.c_void_p], C.c_int),
+    "hp_ensemble_set_variant": ([C.c_void_p, C.c_int32], C.c_int),
+    "hp_ensemble_autotune": ([C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p], C.c_int),
+    "hp_ensemble_sweep": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "hp_get_sweep_counter": ([C.c_void_p, C.POINTER(C.c_uint64)], C.c_int),
     "hp_set_sweep_counter": ([C.c_void_p, C.c_uint64], C.c_int),
     "hp_grain_counts": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -174,6 +182,48 @@ def hp_cp_step(prm, seed, grain, quat, t0, n_incr, eps_p, gamma, g, sigma=None, 
                             C.byref(st), _ptr(sigma), _ptr(w), _ptr(erho), _ptr(b), _stream(stream)))
 
 
+def hp_sweep_variants(nbr):
+    n = C.c_int32(0)
+    _check(lib().hp_sweep_variants(int(nbr), C.byref(n)))
+    return n.value
+
+
+class Ensemble:
+    """Independent lattices swept together (an ``hp_ensemble``)."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m._h for m in self.members])
+        h = C.c_void_p()
+        _check(lib().hp_ensemble_create(arr, len(self.members), C.byref(h)))
+        self._h = h
+        self.nbr = self.members[0].nbr
+
+    def close(self):
+        if self._h:
+            lib().hp_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def hp_ensemble_set_variant(self, v):
+        _check(lib().hp_ensemble_set_variant(self._h, int(v)))
+
+    def hp_ensemble_autotune(self, n_mcs=2, stream=None):
+        n = hp_sweep_variants(self.nbr)
+        ms = np.zeros(max(n, 1), dtype=np.float32)
+        ch = C.c_int32(0)
+        _check(lib().hp_ensemble_autotune(self._h, int(n_mcs), ms.ctypes.data, C.byref(ch), _stream(stream)))
+        return ch.value, ms
+
+    def hp_ensemble_sweep(self, n_mcs, stream=None):
+        _check(lib().hp_ensemble_sweep(self._h, int(n_mcs), _stream(stream)))
+
+
 class Lattice:
     """One periodic Potts lattice (an ``hp_handle``)."""
 
@@ -221,6 +271,17 @@ class Lattice:
 
     def hp_set_sweep_kernel(self, kind):
         _check(lib().hp_set_sweep_kernel(self._h, int(kind)))
+
+    def hp_set_sweep_variant(self, v):
+        _check(lib().hp_set_sweep_variant(self._h, int(v)))
+
+    def hp_sweep_autotune(self, n_mcs=4, stream=None):
+        """Time every tile variant; returns (chosen, per-variant ms)."""
+        n = hp_sweep_variants(self.nbr)
+        ms = np.zeros(max(n, 1), dtype=np.float32)
+        ch = C.c_int32(0)
+        _check(lib().hp_sweep_autotune(self._h, int(n_mcs), ms.ctypes.data, C.byref(ch), _stream(stream)))
+        return ch.value, ms
 
     def hp_sweep(self, n_mcs, stream=None):
         _check(lib().hp_sweep(self._h, int(n_mcs), _stream(stream)))
