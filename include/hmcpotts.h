@@ -259,6 +259,35 @@ HP_API int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream);
 HP_API int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat, uint32_t t0,
                int32_t n_incr, hp_cp_state* st, float* sigma, float* w, float* erho, int32_t* b, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Learned field surrogate: 11 -> 64 -> 64 -> 64 -> 2 perceptron with GELU,    */
+/* BF16 operands and FP32 accumulation on the tensor cores.  It maps a grain's */
+/* orientation and the load state to the elastic energy density and the       */
+/* dislocation energy of Eq. (4) that the crystal plasticity of Sec. 2 would   */
+/* produce, so the driving field can be refreshed per grain.                   */
+/* Parameters: one FP32 device buffer of hp_mlp_param_count() floats, in the   */
+/* order W1[64][11], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[2][64],*/
+/* b4[2] (W_l maps layer l-1 to layer l; rows are output features).            */
+/* Inputs X: device float[M][11]; targets T and outputs Y: device float[M][2]. */
+/* ------------------------------------------------------------------------ */
+HP_API int hp_mlp_param_count(int64_t* n);
+/* Y = MLP(X): inputs, weights and hidden activations rounded to BF16, every sum
+ * in FP32.  Asynchronous; a tensor-core wait that runs out of time is reported
+ * by hp_mlp_status.                                                          */
+HP_API int hp_mlp_forward(const float* params, const float* X, int64_t M, float* Y, void* stream);
+/* grads (device float[param_count], overwritten) = dL/dparams and *loss (device
+ * float, may be NULL) = L for L = 1/(2M) sum_rows sum_outputs (y - t)^2.      */
+HP_API int hp_mlp_gradients(const float* params, const float* X, const float* T, int64_t M, float* grads,
+                            float* loss, void* stream);
+/* One Adam step (Kingma & Ba) on the FP32 master weights: m, v (device float
+ * [param_count]) are the moment estimates, step counts from 1.               */
+HP_API int hp_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr, float beta1,
+                       float beta2, float eps, void* stream);
+/* Synchronous: HP_ERR_TIMEOUT (and *timed_out = 1) if any surrogate kernel
+ * since the last call gave up waiting for its tensor-core operations; clears
+ * the flag.                                                                  */
+HP_API int hp_mlp_status(int32_t* timed_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,678 @@
+// Learned field surrogate: 11 -> 64 -> 64 -> 64 -> 2 perceptron with GELU,
+// BF16 operands and FP32 accumulation on the 5th-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory).  It stands in for the
+// per-material-point crystal plasticity of Sec. 2 (elastic energy density and
+// dislocation energy, Eq. (4)) when the driving field is refreshed.
+//
+// Parameters (FP32 master copy, one buffer, this order):
+//   W1 [64][11], b1[64], W2 [64][64], b2[64], W3 [64][64], b3[64], W4 [2][64], b4[2]
+// Forward:  h_l = bf16(GELU(h_{l-1} W_l^T + b_l)), y = h_3 W4^T + b4, with x,
+// W and h rounded to BF16 and every sum accumulated in FP32.
+// Training: L = 1/(2B) sum (y - t)^2; dz_l = (dh_l) * GELU'(z_l); dW_l = dz_l^T h_{l-1};
+// dh_{l-1} = dz_l W_l; then Adam on the FP32 master weights.
+//
+// Tensor-core layout: operands in shared memory use the canonical K-major
+// layout without swizzle -- 8x8 BF16 core matrices of 128 contiguous bytes,
+// consecutive along K (leading byte offset 128), row groups of 8 rows
+// 16*K bytes apart (stride byte offset).  One CTA = 4 warps = one 128-row tile
+// at a time (row r = thread r = TMEM lane r).  A single thread issues the
+// MMAs and commits them to an mbarrier; all waits are bounded by a clock
+// budget after which the kernel raises an error flag and leaves cleanly.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hp {
+namespace {
+
+constexpr int IN = 11, INP = 16, HID = 64, OUT = 2;
+constexpr int OW1 = 0, OB1 = OW1 + HID * IN, OW2 = OB1 + HID, OB2 = OW2 + HID * HID, OW3 = OB2 + HID,
+              OB3 = OW3 + HID * HID, OW4 = OB3 + HID, OB4 = OW4 + OUT * HID, NPARAM = OB4 + OUT;
+constexpr int TILE = 128, NT = 128;
+constexpr long long kWaitCycles = 1ll << 32;  // about two seconds at the boost clock
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// bounded wait on an mbarrier phase; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+    tmem_ld32(taddr, v);
+    tmem_ld32(taddr + 32, v + 32);
+}
+
+// ---------------------------------------------------------------------------
+// Operand layout helpers
+// ---------------------------------------------------------------------------
+// byte offset of element (r, k) of an R x K BF16 operand, K-major, no swizzle
+__device__ __forceinline__ int canon(int r, int k, int K) {
+    return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+// write a full row of K values (K multiple of 8) into a K-major operand
+template <int K>
+__device__ __forceinline__ void put_row(unsigned char* base, int r, const float* v) {
+#pragma unroll
+    for (int c = 0; c < K / 8; ++c) {
+        __align__(16) __nv_bfloat16 t[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = __float2bfloat16_rn(v[8 * c + j]);
+        *reinterpret_cast<int4*>(base + canon(r, 8 * c, K)) = *reinterpret_cast<const int4*>(t);
+    }
+}
+
+// write value v[i] at (i, col) for i < ROWS of a ROWS x K operand (a column)
+template <int ROWS, int K>
+__device__ __forceinline__ void put_col(unsigned char* base, int col, const float* v) {
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i)
+        *reinterpret_cast<__nv_bfloat16*>(base + canon(i, col, K)) = __float2bfloat16_rn(v[i]);
+}
+
+// stage W [N][Kreal] (FP32, row-major) as an N x KP BF16 K-major operand; zero pad
+__device__ void stage_weight(unsigned char* dst, const float* W, int N, int Kreal, int KP) {
+    for (int idx = threadIdx.x; idx < N * KP; idx += NT) {
+        const int n = idx / KP, k = idx - n * KP;
+        const float v = k < Kreal ? W[n * Kreal + k] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(dst + canon(n, k, KP)) = __float2bfloat16_rn(v);
+    }
+}
+
+// stage W^T: element (n, k) = W[k][n] for W [Kdim][N] (both 64 here)
+__device__ void stage_weight_t(unsigned char* dst, const float* W, int N, int K) {
+    for (int idx = threadIdx.x; idx < N * K; idx += NT) {
+        const int n = idx / K, k = idx - n * K;
+        *reinterpret_cast<__nv_bfloat16*>(dst + canon(n, k, K)) = __float2bfloat16_rn(W[k * N + n]);
+    }
+}
+
+// Sum 64 per-lane values over the 32 lanes of a warp; lane l ends with the sums
+// of features 2l and 2l+1 in v[0], v[1] (a butterfly reduce-scatter).
+__device__ __forceinline__ void warp_reduce_scatter64(float* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 16, half = 32; m >= 1; m >>= 1, half >>= 1) {
+        const bool up = lane & m;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float a = v[i], b = v[i + half];
+            const float send = up ? a : b, keep = up ? b : a;
+            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, m);
+        }
+    }
+}
+
+__device__ __forceinline__ void sync_for_mma() {
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+}
+
+// ---------------------------------------------------------------------------
+// Forward (inference)
+// ---------------------------------------------------------------------------
+struct FwdSmem {
+    alignas(1024) unsigned char w1[HID * INP * 2];
+    alignas(1024) unsigned char w2[HID * HID * 2];
+    alignas(1024) unsigned char w3[HID * HID * 2];
+    alignas(1024) unsigned char x[TILE * INP * 2];
+    alignas(1024) unsigned char h[TILE * HID * 2];
+    float b1[HID], b2[HID], b3[HID], w4[OUT * HID], b4[OUT];
+    alignas(8) unsigned long long mbar;
+    uint32_t tmem;
+    int bad;
+};
+
+__global__ void __launch_bounds__(NT) k_mlp_fwd(const float* __restrict__ P, const float* __restrict__ X, int64_t M,
+                                                float* __restrict__ Y, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    FwdSmem& S = *reinterpret_cast<FwdSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) tmem_alloc(saddr(&S.tmem), 64);
+    if (tid == 0) {
+        mbar_init(saddr(&S.mbar));
+        S.bad = 0;
+    }
+    stage_weight(S.w1, P + OW1, HID, IN, INP);
+    stage_weight(S.w2, P + OW2, HID, HID, HID);
+    stage_weight(S.w3, P + OW3, HID, HID, HID);
+    for (int i = tid; i < HID; i += NT) {
+        S.b1[i] = P[OB1 + i];
+        S.b2[i] = P[OB2 + i];
+        S.b3[i] = P[OB3 + i];
+    }
+    for (int i = tid; i < OUT * HID; i += NT) S.w4[i] = bf16r(P[OW4 + i]);
+    if (tid < OUT) S.b4[tid] = P[OB4 + tid];
+    sync_for_mma();
+    const uint32_t tm = S.tmem;
+    const uint32_t mbar = saddr(&S.mbar);
+    const uint32_t lane_base = tm + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    const int64_t ntiles = (M + TILE - 1) / TILE;
+    bool ok = true;
+    float v[HID];
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int64_t row = t * TILE + tid;
+        float xr[INP];
+#pragma unroll
+        for (int k = 0; k < INP; ++k) xr[k] = (k < IN && row < M) ? X[row * IN + k] : 0.0f;
+        put_row<INP>(S.x, tid, xr);
+        sync_for_mma();
+        // layer 1
+        if (tid == 0) {
+            mma(tm, sdesc(saddr(S.x), 128, INP * 16), sdesc(saddr(S.w1), 128, INP * 16), idesc_bf16(TILE, HID), 0);
+            mma_commit(mbar);
+        }
+        ok = mbar_wait(mbar, phase);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        fence_after();
+        tmem_ld64(lane_base, v);
+#pragma unroll
+        for (int k = 0; k < HID; ++k) v[k] = gelu(v[k] + S.b1[k]);
+        put_row<HID>(S.h, tid, v);
+        sync_for_mma();
+        // layers 2 and 3
+        for (int l = 0; l < 2 && ok; ++l) {
+            if (tid == 0) {
+                const unsigned char* w = l == 0 ? S.w2 : S.w3;
+#pragma unroll
+                for (int kk = 0; kk < HID / 16; ++kk)
+                    mma(tm, sdesc(saddr(S.h) + 256 * kk, 128, HID * 16), sdesc(saddr(w) + 256 * kk, 128, HID * 16),
+                        idesc_bf16(TILE, HID), kk > 0);
+                mma_commit(mbar);
+            }
+            ok = mbar_wait(mbar, phase);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) { ok = false; break; }
+            fence_after();
+            tmem_ld64(lane_base, v);
+            const float* b = l == 0 ? S.b2 : S.b3;
+#pragma unroll
+            for (int k = 0; k < HID; ++k) v[k] = gelu(v[k] + b[k]);
+            if (l == 0) {
+                put_row<HID>(S.h, tid, v);
+                sync_for_mma();
+            }
+        }
+        if (!ok) break;
+        // output layer on CUDA cores with BF16-rounded activations and weights
+        float y0 = S.b4[0], y1 = S.b4[1];
+#pragma unroll
+        for (int k = 0; k < HID; ++k) {
+            const float h = bf16r(v[k]);
+            y0 = fmaf(h, S.w4[k], y0);
+            y1 = fmaf(h, S.w4[HID + k], y1);
+        }
+        if (row < M) {
+            Y[row * OUT + 0] = y0;
+            Y[row * OUT + 1] = y1;
+        }
+        fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tm, 64);
+}
+
+// ---------------------------------------------------------------------------
+// Training: gradients of L over a batch (accumulated into grads and loss)
+// ---------------------------------------------------------------------------
+struct TrainSmem {
+    alignas(1024) unsigned char w1[HID * INP * 2];   // B, layer 1 (N=64, K=16)
+    alignas(1024) unsigned char w2[HID * HID * 2];   // B, layer 2
+    alignas(1024) unsigned char w3[HID * HID * 2];   // B, layer 3
+    alignas(1024) unsigned char w2t[HID * HID * 2];  // B of dh1 = dz2 W2 (N = in, K = out)
+    alignas(1024) unsigned char w3t[HID * HID * 2];  // B of dh2 = dz3 W3
+    alignas(1024) unsigned char x[TILE * INP * 2];   // A, layer 1
+    alignas(1024) unsigned char xt[INP * TILE * 2];  // B of dW1 (N = 16 inputs, K = 128 rows)
+    alignas(1024) unsigned char h1[TILE * HID * 2];  // A, layer 2
+    alignas(1024) unsigned char h2[TILE * HID * 2];  // A, layer 3
+    alignas(1024) unsigned char h1t[HID * TILE * 2]; // B of dW2 (N = 64, K = 128 rows)
+    alignas(1024) unsigned char h2t[HID * TILE * 2]; // B of dW3
+    alignas(1024) unsigned char dz[TILE * HID * 2];  // A of dh = dz W (K = out features)
+    alignas(1024) unsigned char dzt[TILE * TILE * 2];// A of dW (M = 128: 64 features + 64 zero rows, K = rows)
+    float b1[HID], b2[HID], b3[HID], w4[OUT * HID], b4[OUT];
+    float gb1[HID], gb2[HID], gb3[HID], gw4[OUT * HID], gb4[OUT], loss;
+    alignas(8) unsigned long long mbar;
+    uint32_t tmem;
+};
+
+// TMEM columns
+constexpr uint32_t CZ1 = 0, CZ2 = 64, CZ3 = 128, CDH = 192, CDW3 = 256, CDW2 = 320, CDW1 = 384;
+
+__global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P, const float* __restrict__ X,
+                                                     const float* __restrict__ T, int64_t M, float inv_batch,
+                                                     float* __restrict__ grads, float* __restrict__ loss, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(saddr(&S.tmem), 512);
+    if (tid == 0) {
+        mbar_init(saddr(&S.mbar));
+        S.loss = 0.0f;
+    }
+    stage_weight(S.w1, P + OW1, HID, IN, INP);
+    stage_weight(S.w2, P + OW2, HID, HID, HID);
+    stage_weight(S.w3, P + OW3, HID, HID, HID);
+    stage_weight_t(S.w2t, P + OW2, HID, HID);
+    stage_weight_t(S.w3t, P + OW3, HID, HID);
+    for (int i = tid; i < TILE * TILE * 2 / 16; i += NT) reinterpret_cast<int4*>(S.dzt)[i] = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < HID; i += NT) {
+        S.b1[i] = P[OB1 + i];
+        S.b2[i] = P[OB2 + i];
+        S.b3[i] = P[OB3 + i];
+        S.gb1[i] = S.gb2[i] = S.gb3[i] = 0.0f;
+    }
+    for (int i = tid; i < OUT * HID; i += NT) {
+        S.w4[i] = bf16r(P[OW4 + i]);
+        S.gw4[i] = 0.0f;
+    }
+    if (tid < OUT) {
+        S.b4[tid] = P[OB4 + tid];
+        S.gb4[tid] = 0.0f;
+    }
+    sync_for_mma();
+    const uint32_t tm = S.tmem;
+    const uint32_t mbar = saddr(&S.mbar);
+    const uint32_t lb = tm + ((uint32_t)(warp * 32) << 16);
+    uint32_t phase = 0;
+    const int64_t ntiles = (M + TILE - 1) / TILE;
+    bool ok = true;
+    uint32_t first = 1;  // first tile of this CTA: weight-gradient accumulators start from zero
+    float v[HID], z[HID];
+    float my_loss = 0.0f, gb4_0 = 0.0f, gb4_1 = 0.0f;
+
+    auto wait_mma = [&]() -> bool {
+        const bool w = mbar_wait(mbar, phase);
+        phase ^= 1;
+        const bool any_bad = __syncthreads_or(!w);
+        fence_after();
+        return !any_bad;
+    };
+
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int64_t row = t * TILE + tid;
+        const bool valid = row < M;
+        {
+            float xr[INP];
+#pragma unroll
+            for (int k = 0; k < INP; ++k) xr[k] = (k < IN && valid) ? X[row * IN + k] : 0.0f;
+            put_row<INP>(S.x, tid, xr);
+            put_col<INP, TILE>(S.xt, tid, xr);
+        }
+        sync_for_mma();
+        // ---- forward ------------------------------------------------------
+        if (tid == 0) {
+            mma(tm + CZ1, sdesc(saddr(S.x), 128, INP * 16), sdesc(saddr(S.w1), 128, INP * 16), idesc_bf16(TILE, HID), 0);
+            mma_commit(mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        tmem_ld64(lb + CZ1, v);
+#pragma unroll
+        for (int k = 0; k < HID; ++k) v[k] = gelu(v[k] + S.b1[k]);
+        put_row<HID>(S.h1, tid, v);
+        put_col<HID, TILE>(S.h1t, tid, v);
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma(tm + CZ2, sdesc(saddr(S.h1) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w2) + 256 * kk, 128, HID * 16),
+                    idesc_bf16(TILE, HID), kk > 0);
+            mma_commit(mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        tmem_ld64(lb + CZ2, v);
+#pragma unroll
+        for (int k = 0; k < HID; ++k) v[k] = gelu(v[k] + S.b2[k]);
+        put_row<HID>(S.h2, tid, v);
+        put_col<HID, TILE>(S.h2t, tid, v);
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma(tm + CZ3, sdesc(saddr(S.h2) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w3) + 256 * kk, 128, HID * 16),
+                    idesc_bf16(TILE, HID), kk > 0);
+            mma_commit(mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        tmem_ld64(lb + CZ3, z);
+        // ---- output layer, loss, dz3 ---------------------------------------
+        float y0 = S.b4[0], y1 = S.b4[1];
+#pragma unroll
+        for (int k = 0; k < HID; ++k) {
+            z[k] += S.b3[k];
+            v[k] = bf16r(gelu(z[k]));  // h3
+            y0 = fmaf(v[k], S.w4[k], y0);
+            y1 = fmaf(v[k], S.w4[HID + k], y1);
+        }
+        float d0 = 0.0f, d1 = 0.0f;
+        if (valid) {
+            const float e0 = y0 - T[row * OUT + 0], e1 = y1 - T[row * OUT + 1];
+            my_loss += e0 * e0 + e1 * e1;
+            d0 = e0 * inv_batch;
+            d1 = e1 * inv_batch;
+        }
+        gb4_0 += d0;
+        gb4_1 += d1;
+        {   // dW4[o][k] = sum_rows d_o h3_k
+            float g[HID];
+#pragma unroll
+            for (int k = 0; k < HID; ++k) g[k] = d0 * v[k];
+            warp_reduce_scatter64(g);
+            atomicAdd(&S.gw4[2 * lane], g[0]);
+            atomicAdd(&S.gw4[2 * lane + 1], g[1]);
+#pragma unroll
+            for (int k = 0; k < HID; ++k) g[k] = d1 * v[k];
+            warp_reduce_scatter64(g);
+            atomicAdd(&S.gw4[HID + 2 * lane], g[0]);
+            atomicAdd(&S.gw4[HID + 2 * lane + 1], g[1]);
+        }
+#pragma unroll
+        for (int k = 0; k < HID; ++k) v[k] = (d0 * S.w4[k] + d1 * S.w4[HID + k]) * gelu_grad(z[k]);  // dz3
+        put_row<HID>(S.dz, tid, v);
+        put_col<HID, TILE>(S.dzt, tid, v);
+        warp_reduce_scatter64(v);
+        atomicAdd(&S.gb3[2 * lane], v[0]);
+        atomicAdd(&S.gb3[2 * lane + 1], v[1]);
+        sync_for_mma();
+        // ---- dh2 = dz3 W3, dW3 += dz3^T h2 ---------------------------------
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma(tm + CDH, sdesc(saddr(S.dz) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w3t) + 256 * kk, 128, HID * 16),
+                    idesc_bf16(TILE, HID), kk > 0);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tm + CDW3, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.h2t) + 256 * kk, 128, TILE * 16),
+                    idesc_bf16(TILE, HID), (kk > 0) | (first ^ 1));
+            mma_commit(mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        tmem_ld64(lb + CDH, v);
+        tmem_ld64(lb + CZ2, z);
+#pragma unroll
+        for (int k = 0; k < HID; ++k) v[k] *= gelu_grad(z[k] + S.b2[k]);  // dz2
+        put_row<HID>(S.dz, tid, v);
+        put_col<HID, TILE>(S.dzt, tid, v);
+        warp_reduce_scatter64(v);
+        atomicAdd(&S.gb2[2 * lane], v[0]);
+        atomicAdd(&S.gb2[2 * lane + 1], v[1]);
+        sync_for_mma();
+        // ---- dh1 = dz2 W2, dW2 += dz2^T h1 ---------------------------------
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma(tm + CDH, sdesc(saddr(S.dz) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w2t) + 256 * kk, 128, HID * 16),
+                    idesc_bf16(TILE, HID), kk > 0);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tm + CDW2, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.h1t) + 256 * kk, 128, TILE * 16),
+                    idesc_bf16(TILE, HID), (kk > 0) | (first ^ 1));
+            mma_commit(mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        tmem_ld64(lb + CDH, v);
+        tmem_ld64(lb + CZ1, z);
+#pragma unroll
+        for (int k = 0; k < HID; ++k) v[k] *= gelu_grad(z[k] + S.b1[k]);  // dz1
+        put_col<HID, TILE>(S.dzt, tid, v);
+        warp_reduce_scatter64(v);
+        atomicAdd(&S.gb1[2 * lane], v[0]);
+        atomicAdd(&S.gb1[2 * lane + 1], v[1]);
+        sync_for_mma();
+        // ---- dW1 += dz1^T x -------------------------------------------------
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                mma(tm + CDW1, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.xt) + 256 * kk, 128, TILE * 16),
+                    idesc_bf16(TILE, INP), (kk > 0) | (first ^ 1));
+            mma_commit(mbar);
+        }
+        if (!(ok = wait_mma())) break;
+        first = 0;
+    }
+    // ---- flush this CTA's gradients ------------------------------------------
+    if (ok && !first) {
+        // weight gradients: TMEM lanes 0..63 (warps 0 and 1) hold dW rows (out features)
+        if (warp < 2) {
+            const int o = tid;  // out feature
+            tmem_ld64(lb + CDW3, v);
+#pragma unroll
+            for (int k = 0; k < HID; ++k) atomicAdd(&grads[OW3 + o * HID + k], v[k]);
+            tmem_ld64(lb + CDW2, v);
+#pragma unroll
+            for (int k = 0; k < HID; ++k) atomicAdd(&grads[OW2 + o * HID + k], v[k]);
+            tmem_ld32(lb + CDW1, v);  // 32 columns: the first 16 hold dW1
+#pragma unroll
+            for (int k = 0; k < IN; ++k) atomicAdd(&grads[OW1 + o * IN + k], v[k]);
+        } else {
+            // keep every warp in the aligned tcgen05.ld pattern
+            tmem_ld64(lb + CDW3, v);
+            tmem_ld64(lb + CDW2, v);
+            tmem_ld32(lb + CDW1, v);
+        }
+        // per-row reductions of the loss and b4 gradient
+        for (int m = 16; m >= 1; m >>= 1) {
+            my_loss += __shfl_xor_sync(0xFFFFFFFFu, my_loss, m);
+            gb4_0 += __shfl_xor_sync(0xFFFFFFFFu, gb4_0, m);
+            gb4_1 += __shfl_xor_sync(0xFFFFFFFFu, gb4_1, m);
+        }
+        if (lane == 0) {
+            atomicAdd(&S.loss, my_loss);
+            atomicAdd(&S.gb4[0], gb4_0);
+            atomicAdd(&S.gb4[1], gb4_1);
+        }
+        __syncthreads();
+        for (int i = tid; i < HID; i += NT) {
+            atomicAdd(&grads[OB1 + i], S.gb1[i]);
+            atomicAdd(&grads[OB2 + i], S.gb2[i]);
+            atomicAdd(&grads[OB3 + i], S.gb3[i]);
+        }
+        for (int i = tid; i < OUT * HID; i += NT) atomicAdd(&grads[OW4 + i], S.gw4[i]);
+        if (tid < OUT) atomicAdd(&grads[OB4 + tid], S.gb4[tid]);
+        if (tid == 0 && loss) atomicAdd(loss, S.loss * 0.5f * inv_batch);
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+// Adam on the FP32 master weights (bias-corrected; t counts from 1)
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+int g_err_dev = -1;
+int* g_err = nullptr;
+
+int error_flag(int** out) {
+    int dev = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    if (!g_err || g_err_dev != dev) {
+        HP_CUDA(cudaMalloc((void**)&g_err, sizeof(int)));
+        HP_CUDA(cudaMemset(g_err, 0, sizeof(int)));
+        g_err_dev = dev;
+    }
+    *out = g_err;
+    return HP_OK;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" int hp_mlp_param_count(int64_t* n) {
+    if (!n) return set_error(HP_ERR_ARG, "hp_mlp_param_count: null argument");
+    *n = NPARAM;
+    return HP_OK;
+}
+
+extern "C" int hp_mlp_forward(const float* params, const float* X, int64_t M, float* Y, void* stream) {
+    if (!params || !X || !Y || M < 0) return set_error(HP_ERR_ARG, "hp_mlp_forward: bad arguments");
+    if (M == 0) return HP_OK;
+    int* err = nullptr;
+    int rc = error_flag(&err);
+    if (rc) return rc;
+    const size_t smem = sizeof(FwdSmem) + 1024;
+    static bool configured = false;
+    if (!configured) {
+        HP_CUDA(cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    const int64_t tiles = (M + TILE - 1) / TILE;
+    const int64_t grid = tiles < 4LL * sm_count() ? tiles : 4LL * sm_count();
+    cudaStream_t s = as_stream(stream);
+    ::hp::count_launch();
+    k_mlp_fwd<<<(unsigned)grid, NT, smem, s>>>(params, X, M, Y, err);
+    HP_LAUNCH_CHECK("k_mlp_fwd");
+    return HP_OK;
+}
+
+extern "C" int hp_mlp_gradients(const float* params, const float* X, const float* T, int64_t M, float* grads,
+                                float* loss, void* stream) {
+    if (!params || !X || !T || !grads || M < 1) return set_error(HP_ERR_ARG, "hp_mlp_gradients: bad arguments");
+    int* err = nullptr;
+    int rc = error_flag(&err);
+    if (rc) return rc;
+    cudaStream_t s = as_stream(stream);
+    HP_CUDA(cudaMemsetAsync(grads, 0, sizeof(float) * NPARAM, s));
+    if (loss) HP_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), s));
+    const size_t smem = sizeof(TrainSmem) + 1024;
+    static bool configured = false;
+    if (!configured) {
+        HP_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    const int64_t tiles = (M + TILE - 1) / TILE;
+    const int64_t grid = tiles < sm_count() ? tiles : sm_count();
+    ::hp::count_launch();
+    k_mlp_train<<<(unsigned)grid, NT, smem, s>>>(params, X, T, M, 1.0f / (float)M, grads, loss, err);
+    HP_LAUNCH_CHECK("k_mlp_train");
+    return HP_OK;
+}
+
+extern "C" int hp_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr, float beta1,
+                           float beta2, float eps, void* stream) {
+    if (!params || !grads || !m || !v || step < 1) return set_error(HP_ERR_ARG, "hp_mlp_adam: bad arguments");
+    const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+    ::hp::count_launch();
+    k_adam<<<(NPARAM + 255) / 256, 256, 0, as_stream(stream)>>>(params, grads, m, v, NPARAM, lr, beta1, beta2, eps, c1, c2);
+    HP_LAUNCH_CHECK("k_adam");
+    return HP_OK;
+}
+
+extern "C" int hp_mlp_status(int32_t* timed_out) {
+    if (!timed_out) return set_error(HP_ERR_ARG, "hp_mlp_status: null argument");
+    int* err = nullptr;
+    int rc = error_flag(&err);
+    if (rc) return rc;
+    int v = 0;
+    HP_CUDA(cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost));
+    *timed_out = v;
+    if (v) HP_CUDA(cudaMemset(err, 0, sizeof(int)));
+    return v ? set_error(HP_ERR_TIMEOUT, "surrogate kernel gave up waiting for the tensor cores") : HP_OK;
+}

@@ -79,6 +79,13 @@ _SIGS = {
     "hp_cp_reset": ([C.POINTER(hp_cp_params), C.POINTER(hp_cp_state), C.c_void_p], C.c_int),
     "hp_cp_step": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                     C.POINTER(hp_cp_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_mlp_param_count": ([C.POINTER(C.c_int64)], C.c_int),
+    "hp_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
+                         C.c_int),
+    "hp_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_float,
+                     C.c_float, C.c_void_p], C.c_int),
+    "hp_mlp_status": ([C.POINTER(C.c_int32)], C.c_int),
 }
 
 
@@ -162,6 +169,32 @@ def hp_texture(G, kind, orient, counts, bins, hist, stream=None):
 def hp_philox(seed, ctr, out, stream=None):
     n = ctr.numel() // 4
     _check(lib().hp_philox(C.c_uint64(seed), _ptr(ctr), n, _ptr(out), _stream(stream)))
+
+
+def hp_mlp_param_count():
+    n = C.c_int64(0)
+    _check(lib().hp_mlp_param_count(C.byref(n)))
+    return n.value
+
+
+def hp_mlp_forward(params, X, Y, stream=None):
+    _check(lib().hp_mlp_forward(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
+
+
+def hp_mlp_gradients(params, X, T, grads, loss=None, stream=None):
+    _check(lib().hp_mlp_gradients(_ptr(params), _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grads), _ptr(loss),
+                                  _stream(stream)))
+
+
+def hp_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().hp_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step), float(lr), float(beta1),
+                             float(beta2), float(eps), _stream(stream)))
+
+
+def hp_mlp_status():
+    v = C.c_int32(0)
+    _check(lib().hp_mlp_status(C.byref(v)))
+    return v.value
 
 
 def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=None):
