@@ -288,6 +288,39 @@ HP_API int hp_mlp_adam(float* params, const float* grads, float* m, float* v, in
  * the flag.                                                                  */
 HP_API int hp_mlp_status(int32_t* timed_out);
 
+/* Fixed normalisation of the surrogate's inputs and targets.                  */
+typedef struct {
+    float stress; /* MPa per unit input (sample-frame stress components)       */
+    float strain; /* slip per unit input (average accumulated slip)            */
+    float w;      /* MJ/m^3 per unit of the first output (elastic energy)      */
+    float erho;   /* MJ/m^3 per unit of the second output (dislocation energy) */
+} hp_sur_scales;
+
+/* Training data from the crystal plasticity itself (Sec. 2): n_orient
+ * orientations (device float[4 n_orient]) each followed through load
+ * increments t = 1..n_incr (Eq. (3)) in K stochastic histories (K material
+ * points, Philox counters n_orient*K apart).  After increment t, with
+ * sigma_hat(t) = population average of the sample-frame stress R sigma R^T and
+ * gamma_hat(t) = average slip, sample (t-1)*n_orient + o is
+ *   X = (f(q_o), sigma_hat(t)/stress, gamma_hat(t)/strain)     (device float[.][11])
+ * where f(q) encodes the orientation by four cubic invariants of the loading
+ * axis d = R(q)^T e_x: |d| sorted in decreasing order and
+ * d1^2 d2^2 + d2^2 d3^2 + d3^2 d1^2 (the Taylor strain is axisymmetric about x,
+ * so only d, modulo the cubic symmetry, matters)
+ *   Y = (<w>_K / w, <E_rho>_K / erho)                           (device float[.][2])
+ * load_out (device float[n_incr][7], may be NULL) receives (sigma_hat, gamma_hat)
+ * unscaled.  Allocates its own work buffers.                                 */
+HP_API int hp_sur_generate(const hp_cp_params* prm, uint64_t seed, const float* quat, int32_t n_orient, int32_t K,
+                           int32_t n_incr, const hp_sur_scales* sc, float* X, float* Y, float* load_out,
+                           void* stream);
+/* Per-grain driving field from the surrogate at one load state (host float[7]
+ * = sigma_hat, gamma_hat): y = MLP(f(q_g), load), e_g = energy_scale (y0 w + y1 erho)
+ * [J], b_g = round-half-even(256 e_g) clamped to +-2^20 into b_out (device
+ * int32[G], the HP_FIELD_GRAIN table); e_out (device float[G]) may be NULL.
+ * Synchronises `stream`.                                                     */
+HP_API int hp_sur_field(const float* params, const float* quat, int32_t G, const float* load, const hp_sur_scales* sc,
+                        double energy_scale, int32_t* b_out, float* e_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

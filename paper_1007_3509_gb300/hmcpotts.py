@@ -42,6 +42,10 @@ class hp_cp_params(C.Structure):
                 ("e_incr", C.c_double), ("energy_scale", C.c_double)]
 
 
+class hp_sur_scales(C.Structure):
+    _fields_ = [("stress", C.c_float), ("strain", C.c_float), ("w", C.c_float), ("erho", C.c_float)]
+
+
 class hp_cp_state(C.Structure):
     _fields_ = [("P", C.c_int64), ("eps_p", C.c_void_p), ("gamma", C.c_void_p), ("g", C.c_void_p)]
 
@@ -86,6 +90,10 @@ _SIGS = {
     "hp_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_float,
                      C.c_float, C.c_void_p], C.c_int),
     "hp_mlp_status": ([C.POINTER(C.c_int32)], C.c_int),
+    "hp_sur_generate": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                         C.POINTER(hp_sur_scales), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_sur_field": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(hp_sur_scales), C.c_double,
+                      C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
 
 
@@ -195,6 +203,20 @@ def hp_mlp_status():
     v = C.c_int32(0)
     _check(lib().hp_mlp_status(C.byref(v)))
     return v.value
+
+
+SUR_SCALES = hp_sur_scales(100.0, 1e-3, 0.01, 0.002)
+
+
+def hp_sur_generate(prm, seed, quat, n_orient, K, n_incr, X, Y, load_out=None, scales=SUR_SCALES, stream=None):
+    _check(lib().hp_sur_generate(C.byref(prm), C.c_uint64(seed), _ptr(quat), int(n_orient), int(K), int(n_incr),
+                                 C.byref(scales), _ptr(X), _ptr(Y), _ptr(load_out), _stream(stream)))
+
+
+def hp_sur_field(params, quat, G, load, energy_scale, b_out, e_out=None, scales=SUR_SCALES, stream=None):
+    ld = np.ascontiguousarray(load, dtype=np.float32)
+    _check(lib().hp_sur_field(_ptr(params), _ptr(quat), int(G), ld.ctypes.data, C.byref(scales),
+                              float(energy_scale), _ptr(b_out), _ptr(e_out), _stream(stream)))
 
 
 def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=None):

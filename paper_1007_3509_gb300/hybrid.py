@@ -1,0 +1,149 @@
+"""Hybrid Monte Carlo drivers: sequences of C-ABI calls, no arithmetic here.
+
+The paper's loop (Sec. 5): apply a load increment, let the Monte Carlo crystal
+plasticity split it into elastic and plastic parts at every material point
+(Sec. 2), convert the resulting energies into the bulk energy of the Potts
+model (Sec. 3), and evolve the microstructure by Monte Carlo steps (Sec. 4).
+Here the load is the Taylor increment of Eq. (3) and the field is refreshed
+every `refresh_every` MCS by `incr_per_refresh` increments.
+
+* plain:     per-material-point MCP (``hp_cp_step``) -> per-point field
+             (``HP_FIELD_POINT``, material-point index carried by the sweep)
+* surrogate: the trained network evaluated once per grain (``hp_sur_field``)
+             -> per-grain field (``HP_FIELD_GRAIN``)
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import hmcpotts as hm
+from . import synth
+
+
+@dataclass
+class HybridConfig:
+    L: tuple = (64, 64, 64)
+    G: int = 300
+    seed: int = 1002
+    kT: float = 0.7
+    n_mcs: int = 500
+    refresh_every: int = 50
+    incr_per_refresh: int = 2
+    e_incr: float = 1e-4
+    energy_scale: float = 7.0  # J per MJ/m^3: population maximum of b near 0.1 J
+
+
+def cp_params_table1(e_incr, energy_scale):
+    c = synth.TABLE1
+    return hm.cp_params(c["C11"], c["C12"], c["C44"], c["tau0"], c["taus"], c["h0"], c["beta"], e_incr,
+                        energy_scale=energy_scale)
+
+
+def _texture(torch, lat, quat, G):
+    counts = torch.empty(G, dtype=torch.int64, device="cuda")
+    alive = torch.empty(1, dtype=torch.int32, device="cuda")
+    lat.hp_grain_counts(counts, alive)
+    bins = torch.empty(2 * G, dtype=torch.int32, device="cuda")
+    hist = torch.empty(24, dtype=torch.int64, device="cuda")
+    hm.hp_texture(G, hm.ORIENT_SO3, quat, counts, bins, hist)
+    h = hist.cpu().numpy().astype(np.float64)
+    n = h[:20].sum()
+    return {"mmax_hist": h[:20] / n, "families": h[20:] / n, "alive": int(alive.item())}
+
+
+def run_plain(torch, cfg: HybridConfig, time_it=True):
+    """Plain hybrid: MCP at every material point at each refresh."""
+    N = int(np.prod(cfg.L))
+    lat = hm.Lattice(3, cfg.L, 26, 256, cfg.seed, cfg.G, hm.FIELD_POINT)
+    q = torch.empty(N, dtype=torch.int32, device="cuda")
+    mp = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.hp_bind(q, mp)
+    quat = torch.empty(cfg.G, 4, dtype=torch.float32, device="cuda")
+    lat.hp_init_voronoi(hm.ORIENT_SO3, quat)
+    grain = q.clone()  # material point p belongs to the grain of site p at the start
+    prm = cp_params_table1(cfg.e_incr, cfg.energy_scale)
+    eps = torch.empty(6 * N, dtype=torch.float32, device="cuda")
+    gam = torch.empty(N, dtype=torch.float32, device="cuda")
+    g = torch.empty(N, dtype=torch.float32, device="cuda")
+    b = torch.empty(N, dtype=torch.int32, device="cuda")
+    hm.hp_cp_reset(prm, N, eps, gam, g)
+    thr, D = hm.hp_build_threshold_table(cfg.kT)
+    lat.hp_set_threshold_table(thr, D)
+    lat.hp_set_field(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_field = 0.0
+    incr = 0
+    for k in range(cfg.n_mcs // cfg.refresh_every):
+        f0 = time.perf_counter()
+        hm.hp_cp_step(prm, cfg.seed, grain, quat, incr, cfg.incr_per_refresh, eps, gam, g, b=b)
+        if time_it:
+            torch.cuda.synchronize()
+        t_field += time.perf_counter() - f0
+        incr += cfg.incr_per_refresh
+        lat.hp_sweep(cfg.refresh_every)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    tex = _texture(torch, lat, quat, cfg.G)
+    lat.close()
+    return {"wall_s": wall, "field_s": t_field, **tex}
+
+
+def train_surrogate(torch, prm, n_orient=16384, K=8, n_incr=20, steps=10000, lr=3e-3, seed=3000, log_every=0):
+    """Generate samples with the MCP kernel and fit the network with the tensor-core kernels.
+    Returns (params tensor, load table [n_incr, 7] (numpy), final loss, history)."""
+    quat = torch.empty(n_orient, 4, dtype=torch.float32, device="cuda")
+    hm.hp_orientations(n_orient, seed, hm.ORIENT_SO3, quat)
+    M = n_orient * n_incr
+    X = torch.empty(M, 11, dtype=torch.float32, device="cuda")
+    Y = torch.empty(M, 2, dtype=torch.float32, device="cuda")
+    load = torch.empty(n_incr, 7, dtype=torch.float32, device="cuda")
+    hm.hp_sur_generate(prm, seed, quat, n_orient, K, n_incr, X, Y, load)
+    init = np.concatenate([p.ravel() for p in synth.mlp_init(seed + 1)]).astype(np.float32)
+    params = torch.from_numpy(init).cuda()
+    n = params.numel()
+    grads = torch.empty_like(params)
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    hist = []
+    for step in range(1, steps + 1):
+        lr_t = lr * (0.02 + 0.98 * 0.5 * (1 + np.cos(np.pi * step / steps)))  # cosine decay
+        hm.hp_mlp_gradients(params, X, Y, grads, loss)
+        hm.hp_mlp_adam(params, grads, m, v, step, lr_t)
+        if log_every and step % log_every == 0:
+            hist.append((step, float(loss.item())))
+    torch.cuda.synchronize()
+    return params, load.cpu().numpy(), float(loss.item()), hist
+
+
+def run_surrogate(torch, cfg: HybridConfig, params, load_table, time_it=True):
+    """Surrogate hybrid: the trained network evaluated once per grain at each refresh."""
+    N = int(np.prod(cfg.L))
+    lat = hm.Lattice(3, cfg.L, 26, 256, cfg.seed, cfg.G, hm.FIELD_GRAIN)
+    q = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.hp_bind(q)
+    quat = torch.empty(cfg.G, 4, dtype=torch.float32, device="cuda")
+    lat.hp_init_voronoi(hm.ORIENT_SO3, quat)
+    b = torch.empty(cfg.G, dtype=torch.int32, device="cuda")
+    thr, D = hm.hp_build_threshold_table(cfg.kT)
+    lat.hp_set_threshold_table(thr, D)
+    lat.hp_set_field(b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_field = 0.0
+    incr = 0
+    for k in range(cfg.n_mcs // cfg.refresh_every):
+        incr += cfg.incr_per_refresh
+        f0 = time.perf_counter()
+        hm.hp_sur_field(params, quat, cfg.G, load_table[min(incr, len(load_table)) - 1], cfg.energy_scale, b)
+        t_field += time.perf_counter() - f0
+        lat.hp_sweep(cfg.refresh_every)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    tex = _texture(torch, lat, quat, cfg.G)
+    lat.close()
+    return {"wall_s": wall, "field_s": t_field, **tex}
