@@ -45,8 +45,16 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-secondary", action="store_true")
-    p.add_argument("--mcs", type=int, default=W.n_mcs, help="MCS per step (default: the workload's 1000)")
-    return p.parse_args()
+    p.add_argument("--mcs", type=int, default=None, help="MCS per step (default: the workload's)")
+    p.add_argument("--variant", type=int, default=None, help="sweep3d: tile variant (default: autotuned)")
+    p.add_argument("--workload", choices=["2d", "3d-cp", "ensemble", "surrogate", "sweep3d"], default="2d",
+                   help="2d: 4096^2 Moore (default line); 3d-cp: 512^3 plasticity-driven hybrid; ensemble: 256 "
+                        "replicas; surrogate: 1024^3 plain vs surrogate time-to-texture")
+    p.add_argument("--no-autotune", action="store_true")
+    a = p.parse_args()
+    if a.mcs is None:
+        a.mcs = {"2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20}[a.workload]
+    return a
 
 
 def peaks():
@@ -131,6 +139,14 @@ class Job:
         self.lat.hp_set_threshold_table(thr, D)
         self.lat.hp_set_field(self.bgrain)
         self.C = [synth.NI_BJ[k] for k in ("C11", "C12", "C44")]
+        self.tuned = None
+
+    def autotune(self):
+        """Pick the fastest tile shape on the initialised lattice (state restored)."""
+        self.lat.hp_init_voronoi(self.hm.ORIENT_SO3, self.quat)
+        self.field()
+        chosen, ms = self.lat.hp_sweep_autotune(8)
+        self.tuned = {"variant": int(chosen), "ms_per_8_mcs": [round(float(x), 3) for x in ms]}
 
     def field(self):
         self.hm.hp_grain_field(self.quat, *self.C, W.sigma, W.k_disl, W.energy_scale, self.bgrain)
@@ -162,6 +178,8 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     hm.lib()
     job = Job(torch, hm, W.seed + rank, args.mcs)
+    if not args.no_autotune:
+        job.autotune()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     for _ in range(args.warmup):
         job.step()
@@ -235,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": W.name, "lattice": list(W.L), "nbr": W.nbr, "colours": 4, "grains": W.G,
                    "kT": W.kT, "mcs_per_step": args.mcs, "field": "per-grain closed form (100 MPa, Ni)",
                    "step": "voronoi init + field + sweep + counts/texture", "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tile": job.tuned},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -302,6 +320,7 @@ def run_secondary(torch, hm):
         lat.hp_set_field(bmp)
         thr, D = hm.hp_build_threshold_table(0.7)
         lat.hp_set_threshold_table(thr, D)
+        chosen, ms = lat.hp_sweep_autotune(4)
         lat.hp_sweep(4)
         torch.cuda.synchronize()
         n = 20
@@ -319,7 +338,8 @@ def run_secondary(torch, hm):
         torch.cuda.empty_cache()
         return {"workload": "3d-512-moore26-point-field", "site_updates_per_s": round(rate, 1),
                 "bytes_per_site_update": bytes_per, "achieved_gbs": round(rate * bytes_per / 1e9, 1),
-                "frac_of_measured_hbm": round(rate * bytes_per / 1e9 / peak, 4), "mcs_timed": n}
+                "frac_of_measured_hbm": round(rate * bytes_per / 1e9 / peak, 4), "mcs_timed": n,
+                "tile": {"variant": int(chosen), "ms_per_4_mcs": [round(float(x), 3) for x in ms]}}
     except Exception as e:  # secondary numbers must not break the main line
         return {"error": str(e)[:200]}
 
@@ -383,8 +403,215 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# other workloads (one JSON line each; not part of the default run)
+# ---------------------------------------------------------------------------
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_3d_cp(args):
+    """512^3, 26 neighbours, 2e5 grains, MCP refresh every 50 MCS (2 increments of 1e-4), kT 0.7."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm, hybrid
+    build.build()
+    torch.cuda.set_device(0)
+    Wc = synth.W3D_CP
+    L, G, N = Wc.L, Wc.G, Wc.N
+    ex = Wc.extra
+    lat = hm.Lattice(3, L, 26, 256, Wc.seed, G, hm.FIELD_POINT)
+    q = torch.empty(N, dtype=torch.int32, device="cuda")
+    mp = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.hp_bind(q, mp)
+    quat = torch.empty(G, 4, dtype=torch.float32, device="cuda")
+    prm = hybrid.cp_params_table1(ex["e_incr"], 7.0)
+    eps = torch.empty(6 * N, device="cuda"); gam = torch.empty(N, device="cuda"); g = torch.empty(N, device="cuda")
+    b = torch.empty(N, dtype=torch.int32, device="cuda")
+    thr, D = hm.hp_build_threshold_table(Wc.kT)
+    lat.hp_set_threshold_table(thr, D)
+    lat.hp_set_field(b)
+    lat.hp_init_voronoi(hm.ORIENT_SO3, quat)
+    grain = q.clone()
+    hm.hp_cp_reset(prm, N, eps, gam, g)
+    hm.hp_cp_step(prm, Wc.seed, grain, quat, 0, 2, eps, gam, g, b=b)
+    chosen, ms = lat.hp_sweep_autotune(2)
+    res = []
+    for rep in range(args.warmup + args.steps):
+        timed = rep >= args.warmup
+        e0, e1 = _events(torch)
+        cp_ms = sw_ms = 0.0
+        e0.record()
+        lat.hp_set_sweep_counter(0)
+        lat.hp_init_voronoi(hm.ORIENT_SO3, quat)
+        grain.copy_(q)
+        hm.hp_cp_reset(prm, N, eps, gam, g)
+        incr = 0
+        for k in range(args.mcs // ex["refresh_every"]):
+            c0, c1 = _events(torch)
+            c0.record()
+            hm.hp_cp_step(prm, Wc.seed, grain, quat, incr, ex["incr_per_refresh"], eps, gam, g, b=b)
+            c1.record()
+            incr += ex["incr_per_refresh"]
+            s0, s1 = _events(torch)
+            s0.record()
+            lat.hp_sweep(ex["refresh_every"])
+            s1.record()
+            torch.cuda.synchronize()
+            cp_ms += c0.elapsed_time(c1)
+            sw_ms += s0.elapsed_time(s1)
+        counts = torch.empty(G, dtype=torch.int64, device="cuda")
+        alive = torch.empty(1, dtype=torch.int32, device="cuda")
+        lat.hp_grain_counts(counts, alive)
+        e1.record()
+        torch.cuda.synchronize()
+        if timed:
+            res.append((e0.elapsed_time(e1), cp_ms, sw_ms))
+    tot = sum(r[0] for r in res) / len(res) / 1e3
+    cp = sum(r[1] for r in res) / len(res) / 1e3
+    sw = sum(r[2] for r in res) / len(res) / 1e3
+    peak, _ = peaks()
+    rate_sw = N * args.mcs / sw
+    print(json.dumps({
+        "metric": "Potts site-updates/s", "value": round(N * args.mcs / tot, 1), "unit": "site-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot * 1e3, 2),
+        "higher_is_better": True, "dtype": "int32 sweep / fp32+fp64 plasticity", "data": "synthetic",
+        "config": {"workload": Wc.name, "lattice": list(L), "grains": G, "kT": Wc.kT, "mcs": args.mcs,
+                   "refresh": "MCP every 50 MCS, 2 increments of 1e-4", "tile": {"variant": int(chosen),
+                   "ms_per_2_mcs": [round(float(x), 3) for x in ms]}},
+        "sweep": {"site_updates_per_s": round(rate_sw, 1), "bytes_per_site_update": 20,
+                  "achieved_gbs": round(rate_sw * 20 / 1e9, 1), "frac_of_measured_hbm": round(rate_sw * 20 / 1e9 / peak, 4),
+                  "seconds": round(sw, 3)},
+        "plasticity": {"point_increments_per_s": round(N * incr / cp, 1), "seconds": round(cp, 3),
+                       "increments": incr, "points": N},
+        "alive_grains": int(alive.item())}))
+
+
+def run_ensemble(args):
+    """256 replicas, edges {64..256}, kT U[0.5,0.9], load U[50,200] MPa, 500-20000 grains, 200 MCS."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm
+    build.build()
+    torch.cuda.set_device(0)
+    members, bufs = [], []
+    C = [synth.NI_BJ[k] for k in ("C11", "C12", "C44")]
+    t0 = time.perf_counter()
+    for m in synth.ensemble_members():
+        L = (m["edge"],) * 3
+        N = m["edge"] ** 3
+        lat = hm.Lattice(3, L, 26, 256, m["seed"], m["G"], hm.FIELD_GRAIN)
+        q = torch.empty(N, dtype=torch.int32, device="cuda")
+        lat.hp_bind(q)
+        quat = torch.empty(m["G"], 4, device="cuda")
+        lat.hp_init_voronoi(hm.ORIENT_SO3, quat)
+        bg = torch.empty(m["G"], dtype=torch.int32, device="cuda")
+        hm.hp_grain_field(quat, *C, m["sigma"], 0.05, 1.0, bg)
+        lat.hp_set_field(bg)
+        thr, D = hm.hp_build_threshold_table(m["kT"])
+        lat.hp_set_threshold_table(thr, D)
+        members.append(lat)
+        bufs.append((q, quat, bg))
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    sites = sum(l.N for l in members)
+    ens = hm.Ensemble(members)
+    chosen, ms = ens.hp_ensemble_autotune(1)
+    times = []
+    for rep in range(args.warmup + args.steps):
+        e0, e1 = _events(torch)
+        e0.record()
+        ens.hp_ensemble_sweep(args.mcs)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t = sum(times) / len(times)
+    rate = sites * args.mcs / t
+    peak, _ = peaks()
+    print(json.dumps({
+        "metric": "Potts site-updates/s", "value": round(rate, 1), "unit": "site-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2), "higher_is_better": True,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "ensemble-256-replicas-3d-moore26", "replicas": len(members), "sites": sites,
+                   "mcs": args.mcs, "launch": "one CUDA graph replay per step (2 batched kernels per MCS)",
+                   "tile": {"variant": int(chosen), "ms_per_mcs": [round(float(x), 3) for x in ms]},
+                   "init_seconds": round(init_s, 2)},
+        "roofline": {"bound": "hbm", "bytes_per_site_update": 8, "achieved": round(rate * 8 / 1e9, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(rate * 8 / 1e9 / peak, 4)}}))
+
+
+def run_surrogate(args):
+    """1024^3, 10^6 grains: plain MCP-driven hybrid vs surrogate-driven hybrid, wall time to 500 MCS
+    (surrogate time includes generating its data and training it) and texture fractions."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm, hybrid
+    build.build()
+    torch.cuda.set_device(0)
+    Wc = synth.W3D_SURROGATE
+    cfg = hybrid.HybridConfig(L=Wc.L, G=Wc.G, seed=Wc.seed, kT=Wc.kT, n_mcs=args.mcs)
+    t0 = time.perf_counter()
+    prm = hybrid.cp_params_table1(cfg.e_incr, cfg.energy_scale)
+    params, load, loss, _ = hybrid.train_surrogate(torch, prm)
+    train_s = time.perf_counter() - t0
+    sur = hybrid.run_surrogate(torch, cfg, params, load)
+    torch.cuda.empty_cache()
+    plain = hybrid.run_plain(torch, cfg)
+    print(json.dumps({
+        "metric": "time-to-texture (s)", "value": round(train_s + sur["wall_s"], 2), "unit": "s",
+        "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": Wc.name, "lattice": list(Wc.L), "grains": Wc.G, "mcs": args.mcs,
+                   "refresh": "every 50 MCS"},
+        "surrogate": {"train_seconds": round(train_s, 2), "run_seconds": round(sur["wall_s"], 2),
+                      "final_loss": loss, "families": [round(x, 5) for x in sur["families"]],
+                      "field_seconds": round(sur["field_s"], 3)},
+        "plain": {"run_seconds": round(plain["wall_s"], 2), "families": [round(x, 5) for x in plain["families"]],
+                  "field_seconds": round(plain["field_s"], 3)},
+        "speedup": round(plain["wall_s"] / (train_s + sur["wall_s"]), 3)}))
+
+
+def run_sweep3d(args):
+    """The 3D 512^3 26-neighbour sweep alone (per-point field, material-point index carried)."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm
+    build.build()
+    torch.cuda.set_device(0)
+    L, N = (512, 512, 512), 512 ** 3
+    lat = hm.Lattice(3, L, 26, 256, 1002, 200_000, hm.FIELD_POINT)
+    q = torch.empty(N, dtype=torch.int32, device="cuda")
+    mp = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.hp_bind(q, mp)
+    lat.hp_init_voronoi(hm.ORIENT_SO3, None)
+    bmp = torch.randint(0, 30, (N,), dtype=torch.int32, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+    lat.hp_set_field(bmp)
+    thr, D = hm.hp_build_threshold_table(0.7)
+    lat.hp_set_threshold_table(thr, D)
+    if args.variant is None:
+        chosen, _ = lat.hp_sweep_autotune(2)
+    else:
+        chosen = args.variant
+        lat.hp_set_sweep_variant(chosen)
+    for _ in range(args.warmup):
+        lat.hp_sweep(1)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch)
+    e0.record()
+    lat.hp_sweep(args.mcs)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    rate = N * args.mcs / s
+    peak, _ = peaks()
+    print(json.dumps({"metric": "Potts site-updates/s", "value": round(rate, 1), "unit": "site-updates/s",
+                      "config": {"workload": "3d-512-moore26-point-field", "variant": int(chosen), "mcs": args.mcs},
+                      "roofline": {"bound": "hbm", "bytes_per_site_update": 20, "achieved": round(rate * 20 / 1e9, 1),
+                                   "peak": peak, "frac": round(rate * 20 / 1e9 / peak, 4)}}))
+
+
 def main():
     args = parse()
+    if args.workload != "2d" and args.impl == "ours":
+        {"3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
+         "sweep3d": run_sweep3d}[args.workload](args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

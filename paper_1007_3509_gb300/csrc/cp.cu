@@ -6,10 +6,12 @@
 //   ee = eps_c - eps_p; s = C : ee                   trial stress (FP32)
 //   tau_a = m_a . s . n_a; zeta = {a : |tau_a| > g}  candidates (FP32)
 //   per candidate, the single-slip return map |tau_a| - x k = g(gamma + x),
-//   k = P:C:P, Voce g(gamma + x) = taus - (taus - g) exp(-h0 x/(taus - tau0)),
-//   solved by Newton in FP64;
+//   k = P:C:P, Voce g(gamma + x) = taus - (taus - g) exp(-h0 x/(taus - tau0));
 //   energy change of the candidate state  dE_a = -x |tau_a| + x^2 k / 2
-//   (E_a = 1/2 ee_a : C : ee_a with ee_a = ee - x sign(tau_a) P_a);
+//   (E_a = 1/2 ee_a : C : ee_a with ee_a = ee - x sign(tau_a) P_a).  For the
+//   selection the candidates use the first Newton iterate from x = 0 in FP32
+//   (relative error ~1e-6 for load steps of 1e-4); the chosen system's map is
+//   then solved to convergence by Newton in FP64 and committed;
 //   p_a = exp(-beta (dE_a - min dE)) / Z (Eq. (1)); R = u0 / 2^32 from
 //   Philox(seed; p, t, tag 1); first a with R < sum_{b<=a} p_b (Eq. (2));
 //   commit eps_p += x sign P, gamma += x, g = g(gamma + x).
@@ -28,6 +30,7 @@ constexpr int kT = 128;
 __constant__ float c_m[12][3];
 __constant__ float c_n[12][3];
 __constant__ double c_k[12];  // P:C:P per system
+__constant__ float c_kf[12];
 
 struct CPArgs {
     float C11, C12, C44;
@@ -115,55 +118,68 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
             if (fabsf(tau[al]) > gres) mask |= 1 << al;
         }
         if (!mask) continue;
-        double x[12], dE[12];
-        double dEmin = 1e300;
-        const double g0 = gres;
+        // candidate energies for the selection (Eq. (1)): the linearised
+        // return map x_a = (|tau_a| - g)/(k_a + dg/dgamma), relative error
+        // about 1e-6 against the converged one, in FP32
+        const float sat32 = (float)(a.taus - (double)gres);
+        const float hg = hard ? sat32 * (float)hr : 0.0f;
+        float dE[12];
+        float dEmin = 3.4e38f;
 #pragma unroll
         for (int al = 0; al < 12; ++al) {
+            dE[al] = 0.0f;
             if (!(mask >> al & 1)) continue;
-            const double at = fabs((double)tau[al]);
-            const double k = c_k[al];
-            double xx;
-            if (!hard) {
-                xx = (at - g0) / k;
-            } else {
-                const double sat = a.taus - g0;  // taus - g
-                xx = (at - g0) / (k + sat * hr);
-#pragma unroll 1
-                for (int it = 0; it < 8; ++it) {
-                    const double ey = exp_neg(hr * xx);
-                    const double f = at - xx * k - (a.taus - sat * ey);
-                    const double fp = -k - sat * hr * ey;
-                    const double dx = f / fp;
-                    xx -= dx;
-                    if (fabs(f) < 1e-13 * a.tau0) break;
-                }
-            }
-            x[al] = xx;
-            dE[al] = -xx * at + 0.5 * xx * xx * k;
-            dEmin = fmin(dEmin, dE[al]);
+            const float at = fabsf(tau[al]);
+            const float k = c_kf[al];
+            const float xx = (at - gres) / (k + hg);
+            dE[al] = -xx * at + 0.5f * xx * xx * k;
+            dEmin = fminf(dEmin, dE[al]);
         }
-        float wgt[12];
         double Z = 0.0;
+        float wgt[12];
 #pragma unroll
         for (int al = 0; al < 12; ++al) {
-            wgt[al] = (mask >> al & 1) ? expf(-a.beta * (float)(dE[al] - dEmin)) : 0.0f;
+            wgt[al] = (mask >> al & 1) ? expf(-a.beta * (dE[al] - dEmin)) : 0.0f;
             Z += (double)wgt[al];
         }
         const uint4 u = draw(a.seed, (uint64_t)p, t, kTagMcp, 0);
         const double Rn = (double)u.x * (1.0 / 4294967296.0);
         double cum = 0.0;
         int pick = -1, last = -1;
+        float tau_pick = 0.0f;
 #pragma unroll
         for (int al = 0; al < 12; ++al) {
             if (!(mask >> al & 1)) continue;
             last = al;
             cum += (double)wgt[al] / Z;
-            if (pick < 0 && Rn < cum) pick = al;
+            if (pick < 0 && Rn < cum) { pick = al; tau_pick = tau[al]; }
         }
-        if (pick < 0) pick = last;
-        const double xs = x[pick];
-        const float sg = tau[pick] > 0.f ? 1.f : -1.f;
+        if (pick < 0) {
+            pick = last;
+#pragma unroll
+            for (int al = 0; al < 12; ++al)
+                if (al == last) tau_pick = tau[al];
+        }
+        // the single-slip return map of the chosen system, converged in FP64
+        const double g0 = gres;
+        const double at = fabs((double)tau_pick);
+        const double k = c_k[pick];
+        double xs;
+        if (!hard) {
+            xs = (at - g0) / k;
+        } else {
+            const double sat = a.taus - g0;
+            xs = (at - g0) / (k + sat * hr);
+#pragma unroll 1
+            for (int it = 0; it < 8; ++it) {
+                const double ey = exp_neg(hr * xs);
+                const double f = at - xs * k - (a.taus - sat * ey);
+                const double fp = -k - sat * hr * ey;
+                xs -= f / fp;
+                if (fabs(f) < 1e-13 * a.tau0) break;
+            }
+        }
+        const float sg = tau_pick > 0.f ? 1.f : -1.f;
         const float m0 = c_m[pick][0], m1 = c_m[pick][1], m2 = c_m[pick][2];
         const float n0 = c_n[pick][0], n1 = c_n[pick][1], n2 = c_n[pick][2];
         const float xf = (float)xs * sg;
@@ -248,6 +264,9 @@ int upload_tables(const hp_cp_params* prm) {
     HP_CUDA(cudaMemcpyToSymbol(c_m, m, sizeof m));
     HP_CUDA(cudaMemcpyToSymbol(c_n, n, sizeof n));
     HP_CUDA(cudaMemcpyToSymbol(c_k, k, sizeof k));
+    float kf[12];
+    for (int i = 0; i < 12; ++i) kf[i] = (float)k[i];
+    HP_CUDA(cudaMemcpyToSymbol(c_kf, kf, sizeof kf));
     g_loaded[0] = prm->C11; g_loaded[1] = prm->C12; g_loaded[2] = prm->C44;
     g_loaded_dev = dev;
     return HP_OK;

@@ -78,6 +78,8 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
     t_field = 0.0
     incr = 0
     for k in range(cfg.n_mcs // cfg.refresh_every):
+        if time_it:
+            torch.cuda.synchronize()
         f0 = time.perf_counter()
         hm.hp_cp_step(prm, cfg.seed, grain, quat, incr, cfg.incr_per_refresh, eps, gam, g, b=b)
         if time_it:
@@ -138,6 +140,8 @@ def run_surrogate(torch, cfg: HybridConfig, params, load_table, time_it=True):
     incr = 0
     for k in range(cfg.n_mcs // cfg.refresh_every):
         incr += cfg.incr_per_refresh
+        if time_it:
+            torch.cuda.synchronize()
         f0 = time.perf_counter()
         hm.hp_sur_field(params, quat, cfg.G, load_table[min(incr, len(load_table)) - 1], cfg.energy_scale, b)
         t_field += time.perf_counter() - f0

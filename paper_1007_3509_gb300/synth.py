@@ -47,10 +47,10 @@ W2D_SMALL = Workload("2d-128-nbr4-g64", 2, (128, 128), 4, 64, 1000, 0.5, 100, fi
 W2D_MOORE = Workload("2d-4096-moore8-g1e4", 2, (4096, 4096), 8, 10_000, 1001, 0.6, 1000, orient_kind=1,
                      field="grain_closed_form", sigma=100.0, k_disl=0.05, energy_scale=1.0)
 W3D_CP = Workload("3d-512-moore26-g2e5-cp", 3, (512, 512, 512), 26, 200_000, 1002, 0.7, 500, orient_kind=1,
-                  field="cp", extra=dict(refresh_every=50, incr_per_refresh=2, e_incr=1e-4, energy_scale=0.25))
+                  field="cp", extra=dict(refresh_every=50, incr_per_refresh=2, e_incr=1e-4, energy_scale=7.0))
 W3D_SURROGATE = Workload("3d-1024-moore26-g1e6-surrogate", 3, (1024, 1024, 1024), 26, 1_000_000, 1004, 0.7, 500,
                          orient_kind=1, field="cp",
-                         extra=dict(refresh_every=50, incr_per_refresh=2, e_incr=1e-4, energy_scale=0.25,
+                         extra=dict(refresh_every=50, incr_per_refresh=2, e_incr=1e-4, energy_scale=7.0,
                                     train_samples=1_000_000, train_seed=3000))
 
 
