@@ -206,13 +206,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     launches = hm.hp_kernel_launches() - launches0
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    max_ms = float(t.item())
-    site_updates = job.N * args.mcs * args.steps * world
-    value = site_updates / (max_ms / 1e3)
+    max_ms, value = aggregate(total_ms, job.N * args.mcs * args.steps, world, "cuda")
 
     # dominant kernel: one fused-plane launch per MCS over N sites
     per_launch_s = statistics.mean(sweep_ms) / 1e3 / args.mcs
@@ -262,6 +256,18 @@ def run_ours(args, rank, world, local_rank):
         "secondary": secondary,
     }
     print(json.dumps(line))
+
+
+def aggregate(local_ms, local_units, world, device):
+    """Whole-job throughput over ranks: every rank processed `local_units`; the
+    job time is the slowest rank's.  Returns (max_ms, units per second)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    max_ms = float(t.item())
+    return max_ms, local_units * world / (max_ms / 1e3)
 
 
 def run_e2e(torch, hm, job, args):

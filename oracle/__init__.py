@@ -63,6 +63,8 @@ def _declare(L):
     L.oracle_threshold_table.argtypes = [dbl, C.c_int, P(u32), i32, P(i32)]
     L.oracle_sweep.argtypes = [C.c_int, P(i64), C.c_int, i32, u64, u32, i32, P(u32), i32,
                                P(i32), P(i32), P(i32), P(i64)]
+    L.oracle_sweep_phase_slab.argtypes = [C.c_int, P(i64), C.c_int, i32, u64, u32, C.c_int, P(u32), i32, i64, i64,
+                                          P(i32), P(i32), P(i32), P(i64)]
     L.oracle_voronoi_seeds.argtypes = [C.c_int, P(i64), i32, u64, P(i64)]
     L.oracle_voronoi_site.argtypes = [C.c_int, P(i64), i32, P(i64), i64]
     L.oracle_voronoi_site.restype = i32
@@ -142,6 +144,18 @@ def sweep(dim, L, nbr, J_fix, seed, sweep0, n_mcs, thr, D, q, b=None, mp=None):
                               int(n_mcs), _p(thr, C.c_uint32), int(D), _p(q, C.c_int32), _p(b, C.c_int32),
                               _p(mp, C.c_int32), C.byref(flips)), "sweep")
     return q, b, mp, flips.value
+
+
+def sweep_phase_slab(dim, L, nbr, J_fix, seed, sweep, colour, thr, D, s0, ns, q, b=None, mp=None):
+    """One colour phase on a slab array of (ns + 2) layers (ghosts included), in place."""
+    Ls = np.array(list(L) + [1] * (3 - len(L)), dtype=np.int64)
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    flips = C.c_int64(0)
+    _check(lib().oracle_sweep_phase_slab(dim, _p(Ls, C.c_int64), nbr, int(J_fix), C.c_uint64(seed), C.c_uint32(sweep),
+                                         int(colour), _p(thr, C.c_uint32), int(D), int(s0), int(ns),
+                                         _p(q, C.c_int32), _p(b, C.c_int32), _p(mp, C.c_int32), C.byref(flips)),
+           "sweep_phase_slab")
+    return flips.value
 
 
 # ----------------------------------------------------------------------------

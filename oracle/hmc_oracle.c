@@ -813,3 +813,72 @@ int oracle_grain_bins(int32_t G, int kind, const float* orient, int32_t* bins, d
     }
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* One colour phase on a slab with ghost layers (the domain decomposition of */
+/* Sec. 4: the lattice is divided among processors, which exchange boundary  */
+/* layers at every half step).  The slab holds global layers                 */
+/* [s0 - 1, s0 + ns + 1) of the slowest axis (y in 2D, z in 3D), periodic;   */
+/* only colour-c sites of the owned layers [s0, s0 + ns) are updated, with   */
+/* the same keyed draws (global site index) as oracle_sweep, so a run over   */
+/* slabs with exchanged ghost layers equals the undecomposed run.            */
+/* q, b, mp: (ns + 2) layers of the slab (b, mp may be NULL).                */
+/* ------------------------------------------------------------------------ */
+int oracle_sweep_phase_slab(int dim, const int64_t* L, int nbr, int32_t J_fix, uint64_t seed, uint32_t sweep,
+                            int colour, const uint32_t* thr, int32_t D, int64_t s0, int64_t ns,
+                            int32_t* q, int32_t* b, int32_t* mp, int64_t* n_flips) {
+    off3 o[26];
+    const int M = neighbourhood(dim, nbr, o);
+    if (!M || !q || !thr || ns < 1) return OR_ERR_ARG;
+    const int64_t Lx = L[0], Ly = L[1], Lz = dim == 3 ? L[2] : 1;
+    const int64_t Ls = dim == 3 ? Lz : Ly;      /* slowest axis */
+    const int64_t layer = dim == 3 ? Lx * Ly : Lx;
+    int64_t flips = 0;
+    for (int64_t t = 0; t < ns; ++t) {
+        const int64_t gs = s0 + t;              /* global layer */
+        for (int64_t r = 0; r < layer; ++r) {
+            const int64_t x = r % Lx, y = dim == 3 ? r / Lx : gs, z = dim == 3 ? gs : 0;
+            if (colour_of(dim, nbr, x, y, z) != colour) continue;
+            const int64_t li = (t + 1) * layer + r;
+            int64_t nb[26];
+            for (int k = 0; k < M; ++k) {
+                const int64_t xx = wrap(x + o[k].dx, Lx);
+                int64_t ll;
+                if (dim == 3) {
+                    const int64_t yy = wrap(y + o[k].dy, Ly);
+                    ll = (t + 1 + o[k].dz) * layer + xx + Lx * yy;
+                } else {
+                    ll = (t + 1 + o[k].dy) * layer + xx;
+                }
+                nb[k] = ll;
+            }
+            const int64_t gi = x + Lx * (y + Ly * z);
+            uint32_t u[4];
+            draw(seed, (uint64_t)gi, sweep, TAG_SWEEP, (uint32_t)colour, u);
+            const int k = (int)(((uint64_t)u[0] * (uint64_t)M) >> 32);
+            const int64_t j = nb[k];
+            const int32_t qi = q[li], qj = q[j];
+            if (qj == qi) continue;
+            int same_old = 0, same_new = 0;
+            for (int n = 0; n < M; ++n) {
+                same_old += q[nb[n]] == qi;
+                same_new += q[nb[n]] == qj;
+            }
+            const int32_t db = b ? (b[j] - b[li]) : 0;
+            const int32_t d = J_fix * (same_old - same_new) + db;
+            int accept;
+            if (d < 0) accept = 1;
+            else if (d > D) accept = 0;
+            else accept = thr[d] == 0xFFFFFFFFu || u[1] < thr[d];
+            if (accept) {
+                q[li] = qj;
+                if (b) b[li] = b[j];
+                if (mp) mp[li] = mp[j];
+                ++flips;
+            }
+        }
+    }
+    (void)Ls;
+    if (n_flips) *n_flips = flips;
+    return OR_OK;
+}
