@@ -226,7 +226,9 @@ struct PlaneCfg {
     static constexpr int PL = WY * WXH;                  // one parity half of a window plane
     static constexpr int NP = NBR == 4 ? 2 : 4;          // colour phases in a plane
     static constexpr bool Z = NBR == 26;
-    static constexpr int QCAP = WXH * WY;                // queue capacity (>= sites of one colour)
+    // queue capacity: at most the sites of one colour in the window -- every row
+    // (2 colours) or every other row (Moore planes), WXH per row
+    static constexpr int QCAP = NBR == 4 ? WXH * WY : WXH * ((WY + 1) / 2);
     static constexpr int planes = Z ? 3 : 1;
     static size_t smem(bool hasmp) {
         return sizeof(int32_t) * (size_t)(2 * PL) * (planes + (hasmp ? 1 : 0)) + sizeof(uint32_t) * QCAP +
@@ -289,9 +291,14 @@ __device__ __forceinline__ void plane_body(const PlaneArgs& a, const int tile, c
     }
     __syncthreads();
 
-    const int lane_x = threadIdx.x & (WXH - 1);  // one warp pair per window row
-    const int row_slot = threadIdx.x / WXH;      // kThreads / WXH rows at a time
-    constexpr int ROWS_PER_PASS = kThreads / WXH;
+    // stage A works on pairs of same-colour sites (half-indices xh, xh+1 of one
+    // parity in one row): their own values and same-parity neighbours are one
+    // aligned 64-bit load per row, their other-parity neighbours a 64-bit and a
+    // 32-bit load per row.
+    constexpr int PAIRS = WXH / 2;
+    const int lane_p = threadIdx.x % PAIRS;
+    const int row_slot = threadIdx.x / PAIRS;
+    constexpr int ROWS_PER_PASS = kThreads / PAIRS;
     const int cz = Z ? 4 * a.zpar : 0;
 
 #pragma unroll
@@ -306,41 +313,62 @@ __device__ __forceinline__ void plane_body(const PlaneArgs& a, const int tile, c
             const int ly = ly0 + RSTEP * row_slot;
             const int px = NBR == 4 ? ((ly + p) & 1) : (p & 1);  // x parity of this colour in row ly
             const bool rowok = ly < hiy;
-            const int lx = 2 * lane_x + px;
-            bool cand = false;
-            int same = 0;
-            if (rowok && lx >= lo && lx < hix) {
+            const int xh = 2 * lane_p;
+            const int lxa = 2 * xh + px, lxb = lxa + 2;
+            const bool va = rowok && lxa >= lo && lxa < hix;
+            const bool vb = rowok && lxb >= lo && lxb < hix;
+            int same_a = 0, same_b = 0;
+            if (va || vb) {
                 const int base = ly * WXH;
-                const int xs = lx >> 1;
-                // same parity column (dx = 0), other parity columns (dx = -1, +1)
-                const int c0 = px * PL + base + xs;
-                const int cl = (px ? 0 : PL) + base + xs - (px ? 0 : 1);
-                const int cr = (px ? 0 : PL) + base + xs + (px ? 1 : 0);
-                const int32_t qi = s_q[c0];
+                const int own = px * PL + base + xh;
+                const int oth = (px ^ 1) * PL + base + xh;
+                const int oth3 = (px ^ 1) * PL + base + (px ? min(xh + 2, WXH - 1) : max(xh - 1, 0));
+                const int2 qq = *reinterpret_cast<const int2*>(s_q + own);
+                // one row of plane P at row offset o; `centre` excludes the site itself
+                auto row = [&](const int32_t* P, int o, bool centre, bool sides, bool middle) {
+                    if (sides) {
+                        const int2 op = *reinterpret_cast<const int2*>(P + oth + o);
+                        const int32_t o3 = P[oth3 + o];
+                        const int32_t al = px ? op.x : o3, ar = px ? op.y : op.x;
+                        const int32_t bl = px ? op.y : op.x, br = px ? o3 : op.y;
+                        same_a += (al == qq.x) + (ar == qq.x);
+                        same_b += (bl == qq.y) + (br == qq.y);
+                    }
+                    if (middle && !centre) {
+                        const int2 sp = *reinterpret_cast<const int2*>(P + own + o);
+                        same_a += sp.x == qq.x;
+                        same_b += sp.y == qq.y;
+                    }
+                };
                 if (NBR == 4) {
-                    same = (s_q[cl] == qi) + (s_q[cr] == qi) + (s_q[c0 - WXH] == qi) + (s_q[c0 + WXH] == qi);
+                    row(s_q, 0, true, true, false);
+                    row(s_q, -WXH, false, false, true);
+                    row(s_q, WXH, false, false, true);
                 } else {
 #pragma unroll
                     for (int dy = -1; dy <= 1; ++dy) {
-                        const int o = dy * WXH;
-                        same += (s_q[cl + o] == qi) + (s_q[cr + o] == qi) + (dy ? (s_q[c0 + o] == qi) : 0);
+                        row(s_q, dy * WXH, dy == 0, true, true);
                         if (Z) {
-                            same += (s_lo[cl + o] == qi) + (s_lo[cr + o] == qi) + (s_lo[c0 + o] == qi);
-                            same += (s_hi[cl + o] == qi) + (s_hi[cr + o] == qi) + (s_hi[c0 + o] == qi);
+                            row(s_lo, dy * WXH, false, true, true);
+                            row(s_hi, dy * WXH, false, true, true);
                         }
                     }
                 }
-                cand = same != M;
             }
-            const unsigned ball = __ballot_sync(0xFFFFFFFFu, cand);
-            if (ball) {
-                const int lane = threadIdx.x & 31;
-                int slot = 0;
-                if (lane == __ffs(ball) - 1) slot = atomicAdd(qn + p, __popc(ball));
-                slot = __shfl_sync(0xFFFFFFFFu, slot, __ffs(ball) - 1);
-                if (cand) {
-                    const int k = slot + __popc(ball & ((1u << lane) - 1));
-                    queue[k] = ((uint32_t)ly << 13) | ((uint32_t)lx << 5) | (uint32_t)same;
+            const int lane = threadIdx.x & 31;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool cand = h == 0 ? (va && same_a != M) : (vb && same_b != M);
+                const unsigned ball = __ballot_sync(0xFFFFFFFFu, cand);
+                if (ball) {
+                    int slot = 0;
+                    if (lane == __ffs(ball) - 1) slot = atomicAdd(qn + p, __popc(ball));
+                    slot = __shfl_sync(0xFFFFFFFFu, slot, __ffs(ball) - 1);
+                    if (cand) {
+                        const int k = slot + __popc(ball & ((1u << lane) - 1));
+                        const int lx = h == 0 ? lxa : lxb, same = h == 0 ? same_a : same_b;
+                        queue[k] = ((uint32_t)ly << 13) | ((uint32_t)lx << 5) | (uint32_t)same;
+                    }
                 }
             }
         }
@@ -437,8 +465,11 @@ __device__ __forceinline__ void plane_body(const PlaneArgs& a, const int tile, c
     }
 }
 
+// at most 51 registers so that five 256-thread CTAs fit on an SM
+constexpr int kPlaneMinBlocks = 5;
+
 template <int NBR, int WX, int TY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kThreads) k_plane(PlaneArgs a) {
+__global__ void __launch_bounds__(kThreads, kPlaneMinBlocks) k_plane(PlaneArgs a) {
     extern __shared__ __align__(16) int32_t smem[];
     plane_body<NBR, WX, TY, FIELD, HASMP>(a, (int)blockIdx.x, (int)blockIdx.y, smem);
 }
@@ -455,7 +486,7 @@ struct BatchArgs {
 };
 
 template <int NBR, int WX, int TY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kThreads) k_plane_batch(BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, kPlaneMinBlocks) k_plane_batch(BatchArgs b) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ PlaneArgs sa;
     __shared__ int s_tile, s_zidx;

@@ -94,7 +94,7 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
     return {"wall_s": wall, "field_s": t_field, **tex}
 
 
-def train_surrogate(torch, prm, n_orient=16384, K=8, n_incr=20, steps=10000, lr=3e-3, seed=3000, log_every=0):
+def train_surrogate(torch, prm, n_orient=16384, K=32, n_incr=20, steps=20000, lr=3e-3, seed=3000, log_every=0):
     """Generate samples with the MCP kernel and fit the network with the tensor-core kernels.
     Returns (params tensor, load table [n_incr, 7] (numpy), final loss, history)."""
     quat = torch.empty(n_orient, 4, dtype=torch.float32, device="cuda")
