@@ -155,8 +155,9 @@ HP_API int hp_set_sweep_kernel(hp_handle* h, int32_t kind);
  * which advances by n_mcs.  On return the state is in the bound buffers.     */
 HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
 
-/* Tile variants of the fused sweep kernel (window width x core height; all
- * give identical lattices).  hp_sweep_variants: how many exist for `nbr`.
+/* Tile variants of the fused sweep kernel (window width x core height, plain
+ * or TMA-fed persistent; all give identical lattices; TMA variants are not
+ * available to ensembles).  hp_sweep_variants: how many exist for `nbr`.
  * hp_set_sweep_variant: choose one (HP_ERR_ARG if not built for the handle's
  * field mode).  hp_sweep_autotune: time every variant for n_mcs MCS on a
  * backup of the bound state (the lattice and sweep counter are restored),
@@ -166,6 +167,9 @@ HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
 HP_API int hp_sweep_variants(int32_t nbr, int32_t* n);
 HP_API int hp_set_sweep_variant(hp_handle* h, int32_t v);
 HP_API int hp_sweep_autotune(hp_handle* h, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream);
+/* Synchronous: HP_ERR_TIMEOUT (and *timed_out = 1) if a TMA-fed sweep kernel
+ * since the last call gave up waiting for one of its copies; clears the flag. */
+HP_API int hp_sweep_status(int32_t* timed_out);
 
 HP_API int hp_get_sweep_counter(const hp_handle* h, uint64_t* out);
 HP_API int hp_set_sweep_counter(hp_handle* h, uint64_t value);

@@ -3,6 +3,7 @@
 // handle layout.)  Nothing here is part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

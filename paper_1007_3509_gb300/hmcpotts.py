@@ -66,6 +66,7 @@ _SIGS = {
     "hp_set_sweep_kernel": ([C.c_void_p, C.c_int32], C.c_int),
     "hp_sweep": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "hp_sweep_variants": ([C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "hp_sweep_status": ([C.POINTER(C.c_int32)], C.c_int),
     "hp_set_sweep_variant": ([C.c_void_p, C.c_int32], C.c_int),
     "hp_sweep_autotune": ([C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p], C.c_int),
     "hp_ensemble_create": ([C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
@@ -235,6 +236,12 @@ def hp_cp_step(prm, seed, grain, quat, t0, n_incr, eps_p, gamma, g, sigma=None, 
     st = hp_cp_state(int(grain.numel()), _ptr(eps_p), _ptr(gamma), _ptr(g))
     _check(lib().hp_cp_step(C.byref(prm), C.c_uint64(seed), _ptr(grain), _ptr(quat), C.c_uint32(t0), int(n_incr),
                             C.byref(st), _ptr(sigma), _ptr(w), _ptr(erho), _ptr(b), _stream(stream)))
+
+
+def hp_sweep_status():
+    v = C.c_int32(0)
+    _check(lib().hp_sweep_status(C.byref(v)))
+    return v.value
 
 
 def hp_sweep_variants(nbr):

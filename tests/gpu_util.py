@@ -14,7 +14,7 @@ def need_gpu():
 
 
 def run_gpu_sweep(torch, hm, dim, L, nbr, J_fix, seed, n_mcs, kT, q0, field_mode, table=None, mp0=None,
-                  kernel=0, zero_rule=0, sweep0=0, chunks=None):
+                  kernel=0, zero_rule=0, sweep0=0, chunks=None, variant=None):
     """Sweep n_mcs on the GPU; returns (q, mp) as numpy arrays."""
     G = int(max(q0.max() + 1, (table.size if (table is not None and field_mode == hm.FIELD_GRAIN) else 1)))
     lat = hm.Lattice(dim, L, nbr, J_fix, seed, G, field_mode)
@@ -27,6 +27,8 @@ def run_gpu_sweep(torch, hm, dim, L, nbr, J_fix, seed, n_mcs, kT, q0, field_mode
     thr, D = hm.hp_build_threshold_table(kT, zero_rule)
     lat.hp_set_threshold_table(thr, D)
     lat.hp_set_sweep_kernel(kernel)
+    if variant is not None:
+        lat.hp_set_sweep_variant(variant)
     lat.hp_set_sweep_counter(sweep0)
     for n in (chunks or [n_mcs]):
         lat.hp_sweep(n)

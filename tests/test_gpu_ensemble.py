@@ -38,8 +38,11 @@ def _oracle_run(oracle, ref, n, sweep0=0):
     return q, mp
 
 
-VARIANT_GEOMS = [(2, (250, 140), 8), (2, (64, 70), 8), (2, (132, 96), 4), (3, (136, 40, 8), 26), (3, (64, 34, 6), 26),
-                 (3, (12, 10, 4), 26)]
+# includes shapes whose tiles are all wrapped (manual loads) and shapes with
+# interior tiles (TMA copies in the TMA-fed variants)
+VARIANT_GEOMS = [(2, (250, 140), 8), (2, (64, 70), 8), (2, (132, 96), 4), (2, (512, 200), 8), (2, (516, 132), 4),
+                 (3, (136, 40, 8), 26), (3, (64, 34, 6), 26), (3, (12, 10, 4), 26), (3, (256, 96, 8), 26),
+                 (3, (200, 72, 6), 26)]
 
 
 @pytest.mark.parametrize("dim,L,nbr", VARIANT_GEOMS)
@@ -54,6 +57,7 @@ def test_every_tile_variant_bit_exact(oracle, dim, L, nbr, mode):
         lat.hp_set_sweep_variant(v)
         lat.hp_sweep(3)
         torch.cuda.synchronize()
+        assert hm.hp_sweep_status() == 0
         q, mp, _ = lat._bufs
         np.testing.assert_array_equal(q.cpu().numpy(), ref_q, err_msg=f"variant {v}")
         if mode == "point":

@@ -94,19 +94,23 @@ def test_sweep_zero_mcs_is_noop():
     np.testing.assert_array_equal(q, q0)
 
 
-def test_sweep_full_size_2d_moore_two_mcs(oracle):
-    """4096^2 Moore lattice, 10^4 Voronoi grains, closed-form grain field: 2 MCS bit-exact."""
+@pytest.mark.parametrize("variant", [0, 1, 3, 4])
+def test_sweep_full_size_2d_moore_two_mcs(oracle, variant):
+    """4096^2 Moore lattice, 10^4 grains, grain field: 2 MCS bit-exact (plain and TMA-fed variants)."""
     torch, hm = need_gpu()
     L, G = (4096, 4096), 10_000
     q0 = synth.blocky_lattice(L, G, 5, block=40)
     bgrain = np.random.default_rng(6).integers(0, 26, size=G).astype(np.int32)
     thr, D = oracle.threshold_table(0.6)
     ref_q, _, _, _ = oracle.sweep(2, L, 8, 256, 1001, 0, 2, thr, D, q0, bgrain[q0], None)
-    q, _ = run_gpu_sweep(torch, hm, 2, L, 8, 256, 1001, 2, 0.6, q0, hm.FIELD_GRAIN, bgrain, None, kernel=0)
+    q, _ = run_gpu_sweep(torch, hm, 2, L, 8, 256, 1001, 2, 0.6, q0, hm.FIELD_GRAIN, bgrain, None, kernel=0,
+                         variant=variant)
     np.testing.assert_array_equal(q, ref_q)
+    assert hm.hp_sweep_status() == 0
 
 
-def test_sweep_full_size_3d_point_field_one_mcs(oracle):
+@pytest.mark.parametrize("variant", [2, 4])
+def test_sweep_full_size_3d_point_field_one_mcs(oracle, variant):
     """512^3 26-neighbour lattice with a per-material-point field: one MCS bit-exact."""
     torch, hm = need_gpu()
     L = (512, 512, 512)
@@ -116,6 +120,7 @@ def test_sweep_full_size_3d_point_field_one_mcs(oracle):
     mp0 = np.arange(N, dtype=np.int32)
     thr, D = oracle.threshold_table(0.7)
     ref_q, _, ref_mp, _ = oracle.sweep(3, L, 26, 256, 1002, 0, 1, thr, D, q0, bmp, mp0)
-    q, mp = run_gpu_sweep(torch, hm, 3, L, 26, 256, 1002, 1, 0.7, q0, hm.FIELD_POINT, bmp, mp0, kernel=0)
+    q, mp = run_gpu_sweep(torch, hm, 3, L, 26, 256, 1002, 1, 0.7, q0, hm.FIELD_POINT, bmp, mp0, kernel=0,
+                          variant=variant)
     np.testing.assert_array_equal(q, ref_q)
     np.testing.assert_array_equal(mp, ref_mp)
