@@ -188,6 +188,22 @@ HP_API int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, void* 
 HP_API int hp_texture(int32_t G, int32_t orient_kind, const float* orient, const int64_t* counts, int32_t* bins,
                int64_t* hist, void* stream);
 
+/* Texture fit of Eq. (10), host FP64: the 90 one-degree angle bins, folded so
+ * that angles above 45 degrees count as negative (Sec. 5), normalised to a
+ * density per degree, and fitted by least squares to
+ * f(phi) = exp(-phi^2 / (2 g^2)) / (g sqrt(2 pi)); returns g [degrees] and the
+ * residual sum of squares (may be NULL).                                     */
+HP_API int hp_texture_fit(const int64_t* hist, int32_t n_bins, double* g_out, double* residual_out);
+
+/* Checkpoint / resume of a handle's lattice state: q (and mp when bound), the
+ * sweep counter and the descriptor, followed by a CRC-32.  Field and threshold
+ * tables are caller inputs and are not stored.  Loading into a handle with a
+ * different descriptor fails with HP_ERR_ARG; a corrupted or truncated file
+ * with HP_ERR_CHECKSUM.  Both synchronise `stream`.  Because every draw is
+ * keyed by (seed, sweep, colour, site), resuming is bit-exact.               */
+HP_API int hp_checkpoint_save(hp_handle* h, const char* path, void* stream);
+HP_API int hp_checkpoint_load(hp_handle* h, const char* path, void* stream);
+
 /* Closed-form per-grain field under uniaxial stress sigma [MPa] along x
  * (Sec. 5): d = loading axis in the crystal frame, E(d) the directional
  * Young's modulus of cubic (C11, C12, C44) [MPa], w = sigma^2/(2 E(d)),

@@ -330,3 +330,28 @@ def mcp_energies(P, sigma, gamma):
     _check(lib().oracle_mcp_energies(C.byref(P), g.size, _p(s, C.c_double), _p(g, C.c_double),
                                      _p(w, C.c_double), _p(er, C.c_double)), "mcp_energies")
     return w, er
+
+
+# ----------------------------------------------------------------------------
+# Texture fit of Eq. (10) (Sec. 5)
+# ----------------------------------------------------------------------------
+def folded_centres():
+    """1-degree bin centres, angles above 45 degrees folded to negative (Sec. 5)."""
+    c = np.arange(90) + 0.5
+    return np.where(c > 45.0, c - 90.0, c)
+
+
+def texture_fit(hist):
+    """Least-squares fit of f(phi) = exp(-phi^2/(2g^2))/(g sqrt(2 pi)) to the folded,
+    per-degree normalised histogram (scipy.optimize.curve_fit)."""
+    from scipy.optimize import curve_fit
+    h = np.asarray(hist, dtype=np.float64)
+    dens = h / h.sum()
+    phi = folded_centres()
+
+    def f(x, g):
+        return np.exp(-x * x / (2.0 * g * g)) / (g * np.sqrt(2.0 * np.pi))
+
+    sd = np.sqrt(max(np.sum(dens * phi * phi), 1e-6))
+    (g,), _ = curve_fit(f, phi, dens, p0=[sd], bounds=(0.5, 2000.0), xtol=1e-14, ftol=1e-14, gtol=1e-14)
+    return float(g)

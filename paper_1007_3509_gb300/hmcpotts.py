@@ -80,6 +80,9 @@ _SIGS = {
     "hp_texture": ([C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_grain_field": ([C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                         C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_texture_fit": ([C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "hp_checkpoint_save": ([C.c_void_p, C.c_char_p, C.c_void_p], C.c_int),
+    "hp_checkpoint_load": ([C.c_void_p, C.c_char_p, C.c_void_p], C.c_int),
     "hp_philox": ([C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "hp_cp_reset": ([C.POINTER(hp_cp_params), C.POINTER(hp_cp_state), C.c_void_p], C.c_int),
     "hp_cp_step": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
@@ -173,6 +176,14 @@ def hp_grain_field(quat, C11, C12, C44, sigma, k_disl, energy_scale, b_out, w_ou
 def hp_texture(G, kind, orient, counts, bins, hist, stream=None):
     _check(lib().hp_texture(int(G), int(kind), _ptr(orient), _ptr(counts), _ptr(bins), _ptr(hist),
                             _stream(stream)))
+
+
+def hp_texture_fit(hist):
+    """Fit g (degrees) of Eq. (10) to a 90-bin angle histogram (host numpy int64)."""
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    g, r = C.c_double(0), C.c_double(0)
+    _check(lib().hp_texture_fit(h.ctypes.data, int(h.size), C.byref(g), C.byref(r)))
+    return g.value, r.value
 
 
 def hp_philox(seed, ctr, out, stream=None):
@@ -355,6 +366,12 @@ class Lattice:
 
     def hp_set_sweep_counter(self, v):
         _check(lib().hp_set_sweep_counter(self._h, C.c_uint64(v)))
+
+    def hp_checkpoint_save(self, path, stream=None):
+        _check(lib().hp_checkpoint_save(self._h, str(path).encode(), _stream(stream)))
+
+    def hp_checkpoint_load(self, path, stream=None):
+        _check(lib().hp_checkpoint_load(self._h, str(path).encode(), _stream(stream)))
 
     def hp_grain_counts(self, counts, alive=None, stream=None):
         _check(lib().hp_grain_counts(self._h, _ptr(counts), _ptr(alive), _stream(stream)))
