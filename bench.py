@@ -47,13 +47,15 @@ def parse():
     p.add_argument("--no-secondary", action="store_true")
     p.add_argument("--mcs", type=int, default=None, help="MCS per step (default: the workload's)")
     p.add_argument("--variant", type=int, default=None, help="sweep3d: tile variant (default: autotuned)")
-    p.add_argument("--workload", choices=["2d", "3d-cp", "ensemble", "surrogate", "sweep3d"], default="2d",
+    p.add_argument("--workload", choices=["2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
+                                          "texture3d"], default="2d",
                    help="2d: 4096^2 Moore (default line); 3d-cp: 512^3 plasticity-driven hybrid; ensemble: 256 "
                         "replicas; surrogate: 1024^3 plain vs surrogate time-to-texture")
     p.add_argument("--no-autotune", action="store_true")
     a = p.parse_args()
     if a.mcs is None:
-        a.mcs = {"2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20}[a.workload]
+        a.mcs = {"2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20, "texture2d": 1000,
+                 "texture3d": 100}[a.workload]
     return a
 
 
@@ -612,8 +614,34 @@ def run_sweep3d(args):
                                    "peak": peak, "frac": round(rate * 20 / 1e9 / peak, 4)}}))
 
 
+def run_texture(args):
+    """Sec. 5 texture experiments: the 2D Gaussian bulk energy of Eq. (9) over a 100-replica
+    ensemble of 500^2 lattices, or the 3D plastic case with the g(t) fit of Eq. (10)."""
+    import torch
+    from paper_1007_3509_gb300 import build, texture
+    build.build()
+    torch.cuda.set_device(0)
+    if args.workload == "texture2d":
+        sl = (0, args.mcs // 10, args.mcs // 3, args.mcs)
+        r = texture.run_gaussian_2d(torch, slices=sl)
+        low = list(range(0, 10)) + list(range(80, 90))
+        print(json.dumps({"workload": "texture2d-gaussian-eq9-100x500^2", "slices": list(sl),
+                          "mean_b_J": [round(x, 5) for x in r["mean_b"]],
+                          "low_energy_fraction": [round(float(h[low].sum() / h.sum()), 4) for h in r["hist"]],
+                          "seconds": round(r["seconds"], 2),
+                          "site_updates_per_s": round(100 * 500 * 500 * args.mcs / r["seconds"], 1)}))
+    else:
+        r = texture.run_plastic_3d(torch, L=(256, 256, 256), G=30000, kT=2.6, n_incr=args.mcs, mcs_per_incr=1,
+                                   e_incr=2e-5, energy_scale=50.0, every=max(1, args.mcs // 10))
+        print(json.dumps({"workload": "texture3d-plastic-zrot-256^3", "t": r["t"],
+                          "g_deg": [round(x, 3) for x in r["g"]], "seconds": round(r["seconds"], 2)}))
+
+
 def main():
     args = parse()
+    if args.workload in ("texture2d", "texture3d") and args.impl == "ours":
+        run_texture(args)
+        return
     if args.workload != "2d" and args.impl == "ours":
         {"3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
          "sweep3d": run_sweep3d}[args.workload](args)

@@ -54,6 +54,8 @@ extern "C" {
 /* Orientation kinds. */
 #define HP_ORIENT_ANGLE 0 /* one rotation angle about z in [0, pi/2), float[G]  */
 #define HP_ORIENT_SO3 1   /* unit quaternion (w,x,y,z) uniform on SO(3), float[4G] */
+#define HP_ORIENT_ZROT 2  /* quaternion (cos t/2, 0, 0, sin t/2) of a rotation by the */
+                          /* HP_ORIENT_ANGLE angle t about z (Sec. 5), float[4G]     */
 
 /* Sweep kernel choice (hp_set_sweep_kernel). */
 #define HP_SWEEP_AUTO 0   /* fused multi-phase tiles where available            */
@@ -184,9 +186,16 @@ HP_API int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, void* 
  * HP_ORIENT_ANGLE: 90 one-degree bins of the angle; bins int32[G].
  * HP_ORIENT_SO3: 20 bins of the max Schmid factor over [0, 0.5] followed by
  * 4 bins (none, <100>, <110>, <111> within 15 degrees of the loading axis x);
- * bins int32[2G]; hist int64[24].                                            */
+ * bins int32[2G]; hist int64[24].  HP_ORIENT_ZROT: 90 one-degree bins of the
+ * rotation angle 2 atan2(z, w); bins int32[G]; hist int64[90].               */
 HP_API int hp_texture(int32_t G, int32_t orient_kind, const float* orient, const int64_t* counts, int32_t* bins,
                int64_t* hist, void* stream);
+
+/* Orientation-dependent Gaussian bulk energy of Eq. (9) (Sec. 5, Fig. 3): a
+ * grain with angle t (device float[G], HP_ORIENT_ANGLE) has orientation
+ * n = floor(t in degrees) + 1 and b = round-half-even(256 scale e(n)) with
+ * e(n) = (32 pi)^(-1/2) exp(-(n - 46)^2 / (2 46^2)) [J]; b_out device int32[G]. */
+HP_API int hp_gaussian_field(int32_t G, const float* angle, double scale, int32_t* b_out, void* stream);
 
 /* Texture fit of Eq. (10), host FP64: the 90 one-degree angle bins, folded so
  * that angles above 45 degrees count as negative (Sec. 5), normalised to a
@@ -251,6 +260,9 @@ typedef struct {
     double G;                /* shear modulus of Eq. (4) [MPa]                  */
     double e_incr;           /* strain increment e of Eq. (3)                   */
     double energy_scale;     /* J (MC units) per MJ/m^3 for the field           */
+    double w_weight;         /* weight of the elastic energy in the field: 1 for */
+                             /* w + E_rho, 0 for the plastic driving force alone */
+                             /* (Sec. 5 suppresses the elastic one)              */
 } hp_cp_params;
 
 /* Material-point state, structure of arrays over P points (device memory):
@@ -274,7 +286,7 @@ HP_API int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream);
  * R = u0/2^32 of Philox(seed; p, t, tag 1).  Afterwards, optionally writes
  * sigma (device float[6][P], NULL to skip), w and E_rho (device float[P] each,
  * NULL to skip; E_rho = 2 g^2/G, w = 1/2 sigma : C^-1 : sigma) and the
- * quantised field b = round-half-even(256 energy_scale (w + E_rho)) (device
+ * quantised field b = round-half-even(256 energy_scale (w_weight w + E_rho)) (device
  * int32[P], NULL to skip) for HP_FIELD_POINT.                                */
 HP_API int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat, uint32_t t0,
                int32_t n_incr, hp_cp_state* st, float* sigma, float* w, float* erho, int32_t* b, void* stream);

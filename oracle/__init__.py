@@ -79,6 +79,7 @@ def _declare(L):
     L.oracle_loading_axis.argtypes = [P(f32), P(dbl)]
     L.oracle_grain_field.argtypes = [i32, P(f32), P(dbl), dbl, dbl, dbl, P(dbl), P(dbl), P(dbl), P(i32)]
     L.oracle_quantise.argtypes = [i64, P(dbl), P(i32)]
+    L.oracle_gaussian_field.argtypes = [i32, P(f32), dbl, P(dbl), P(i32)]
     L.oracle_slip_systems.argtypes = [P(dbl), P(dbl)]
     L.oracle_mcp_increment.argtypes = [P(CPParams), u64, i64, u32, P(f32), P(dbl), P(dbl), P(dbl),
                                        P(dbl), P(dbl), P(i32), P(i32)]
@@ -190,6 +191,7 @@ def voronoi(dim, L, G, seed):
 
 
 def orientations(G, seed, kind):
+    """kind 0: angle about z; 1: SO(3)-uniform quaternion; 2: quaternion of the kind-0 angle about z."""
     out = np.empty(G * (1 if kind == 0 else 4), dtype=np.float32)
     _check(lib().oracle_orientations(G, C.c_uint64(seed), kind, _p(out, C.c_float)), "orientations")
     return out if kind == 0 else out.reshape(G, 4)
@@ -210,16 +212,16 @@ def grain_counts(q, G):
 def grain_bins(orient, kind):
     o = np.ascontiguousarray(orient, dtype=np.float32)
     G = o.shape[0]
-    bins = np.empty(G * (1 if kind == 0 else 2), dtype=np.int32)
+    bins = np.empty(G * (1 if kind != 1 else 2), dtype=np.int32)
     near = np.empty(G, dtype=np.float64)
     _check(lib().oracle_grain_bins(G, kind, _p(o, C.c_float), _p(bins, C.c_int32), _p(near, C.c_double)),
            "grain_bins")
-    return (bins if kind == 0 else bins.reshape(G, 2)), near
+    return (bins if kind != 1 else bins.reshape(G, 2)), near
 
 
 def histogram(counts, bins, kind):
     """Area-weighted texture histogram: hist[b] = sum of counts of grains in bin b."""
-    if kind == 0:
+    if kind != 1:
         h = np.zeros(90, dtype=np.int64)
         np.add.at(h, bins, counts)
     else:
@@ -260,6 +262,15 @@ def grain_field(quat, Cc, sigma, k_disl, energy_scale):
                                     float(energy_scale), _p(w, C.c_double), _p(mm, C.c_double),
                                     _p(e, C.c_double), _p(b, C.c_int32)), "grain_field")
     return w, mm, e, b
+
+
+def gaussian_field(angle, scale=1.0):
+    """Eq. (9) per grain from its angle: returns (e [J], quantised b)."""
+    a = np.ascontiguousarray(angle, dtype=np.float32)
+    e = np.empty(a.size)
+    b = np.empty(a.size, dtype=np.int32)
+    lib().oracle_gaussian_field(a.size, _p(a, C.c_float), float(scale), _p(e, C.c_double), _p(b, C.c_int32))
+    return e, b
 
 
 def quantise(e):

@@ -302,6 +302,8 @@ int oracle_voronoi(int dim, const int64_t* L, int32_t G, uint64_t seed, int32_t*
 /* Grain orientations from Philox(seed; g, 0, TAG_VORONOI<<24 | 1).
  * kind 0: single rotation angle about z, angle = (u0 / 2^32) * pi/2 (the
  *         paper's one-angle grains, Sec. 5), rounded to FP32.
+ * kind 2: the kind-0 angle t as the quaternion (cos t/2, 0, 0, sin t/2) of a
+ *         rotation about z, rounded to FP32.
  * kind 1: unit quaternion (w,x,y,z) uniform on SO(3) by Shoemake's method
  *         ("Uniform random rotations", Graphics Gems III, 1992) from
  *         u1,u2,u3 = u0,u1,u2 / 2^32, computed in FP64, rounded to FP32:
@@ -314,6 +316,13 @@ int oracle_orientations(int32_t G, uint64_t seed, int kind, float* out) {
         draw(seed, (uint64_t)g, 0, TAG_VORONOI, 1, u);
         if (kind == 0) {
             out[g] = (float)(((double)u[0] / two32) * (pi / 2.0));
+        } else if (kind == 2) {
+            /* the same angle as kind 0, as the quaternion of a rotation about z */
+            const double t = ((double)u[0] / two32) * (pi / 2.0);
+            out[4 * g + 0] = (float)cos(0.5 * t);
+            out[4 * g + 1] = 0.0f;
+            out[4 * g + 2] = 0.0f;
+            out[4 * g + 3] = (float)sin(0.5 * t);
         } else if (kind == 1) {
             const double u1 = (double)u[0] / two32, u2 = (double)u[1] / two32, u3 = (double)u[2] / two32;
             const double a = sqrt(1.0 - u1), c = sqrt(u1);
@@ -759,7 +768,8 @@ int oracle_mcp_energies(const oracle_cp_params* P, int64_t npts, const double* s
 
 /* ------------------------------------------------------------------------ */
 /* Texture bins per grain (Sec. 5 orientation distributions).                */
-/* kind 0 (one rotation angle about z): bin = floor(angle * 180/pi), clamped */
+/* kind 0 (one rotation angle about z) and kind 2 (its quaternion, angle      */
+/*        2 atan2(z, w)): bin = floor(angle * 180/pi), clamped               */
 /*        to 0..89 (1 degree bins over [0, 90)).                             */
 /* kind 1 (SO(3) quaternion): bins[2g] = floor(m_max / 0.5 * 20) clamped to  */
 /*        0..19; bins[2g+1] = 20 + family, family 1/2/3 when the loading     */
@@ -771,8 +781,10 @@ int oracle_grain_bins(int32_t G, int kind, const float* orient, int32_t* bins, d
     const double pi = 3.14159265358979323846;
     const double c15 = cos(15.0 * pi / 180.0);
     for (int32_t g = 0; g < G; ++g) {
-        if (kind == 0) {
-            const double deg = (double)orient[g] * (180.0 / pi);
+        if (kind == 0 || kind == 2) {
+            const double t = kind == 0 ? (double)orient[g]
+                                       : 2.0 * atan2((double)orient[4 * g + 3], (double)orient[4 * g]);
+            const double deg = t * (180.0 / pi);
             double f = floor(deg);
             int b = (int)f;
             if (b < 0) b = 0;
@@ -881,4 +893,17 @@ int oracle_sweep_phase_slab(int dim, const int64_t* L, int nbr, int32_t J_fix, u
     (void)Ls;
     if (n_flips) *n_flips = flips;
     return OR_OK;
+}
+
+/* Orientation-dependent Gaussian bulk energy, Eq. (9): orientation
+ * n = floor(angle in degrees) + 1 and e = (32 pi)^(-1/2) exp(-(n-46)^2/(2 46^2)). */
+void oracle_gaussian_field(int32_t G, const float* angle, double scale, double* e, int32_t* b) {
+    const double pi = 3.14159265358979323846;
+    for (int32_t g = 0; g < G; ++g) {
+        int bin = (int)floor((double)angle[g] * (180.0 / pi));
+        bin = bin < 0 ? 0 : (bin > 89 ? 89 : bin);
+        const double n = bin + 1.0;
+        e[g] = scale * exp(-(n - 46.0) * (n - 46.0) / (2.0 * 46.0 * 46.0)) / sqrt(32.0 * pi);
+        b[g] = (int32_t)nearbyint(256.0 * e[g]);
+    }
 }

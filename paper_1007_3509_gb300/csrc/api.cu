@@ -110,7 +110,7 @@ extern "C" int hp_bind(hp_handle* h, int32_t* q, int32_t* mp) {
 extern "C" int hp_init_voronoi(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, void* stream) {
     if (!h) return set_error(HP_ERR_ARG, "hp_init_voronoi: null handle");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_init_voronoi: no lattice bound");
-    if (orient && orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_SO3)
+    if (orient && (orient_kind < HP_ORIENT_ANGLE || orient_kind > HP_ORIENT_ZROT))
         return set_error(HP_ERR_ARG, "hp_init_voronoi: bad orient_kind");
     return voronoi_run(h, orient_kind, orient, seed_pos, as_stream(stream));
 }

@@ -17,7 +17,7 @@
 //   commit eps_p += x sign P, gamma += x, g = g(gamma + x).
 // After the last increment: sigma = C : (eps_c - eps_p); E_rho = 2 g^2 / G
 // (Eq. (4) with sigma_f = g; the Burgers vector cancels); w = 1/2 sigma : ee;
-// b = round-half-even(256 scale (w + E_rho)) clamped to +-2^20.
+// b = round-half-even(256 scale (w_weight w + E_rho)) clamped to +-2^20.
 #include <math.h>
 
 #include "common.cuh"
@@ -39,6 +39,7 @@ struct CPArgs {
     float G;
     float e;
     float scale;
+    float w_weight;
     uint64_t seed;
     const int32_t* grain;
     const float* quat;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         if (a.w) a.w[p] = w;
         if (a.erho) a.erho[p] = er;
         if (a.b) {
-            float v = rintf(256.0f * a.scale * (w + er));
+            float v = rintf(256.0f * a.scale * (a.w_weight * w + er));
             v = fminf(fmaxf(v, -1048576.0f), 1048576.0f);
             a.b[p] = (int32_t)v;
         }
@@ -300,6 +301,7 @@ extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t*
     a.C11 = (float)prm->C11; a.C12 = (float)prm->C12; a.C44 = (float)prm->C44;
     a.tau0 = prm->tau0; a.taus = prm->taus; a.h0 = prm->h0;
     a.beta = (float)prm->beta; a.G = (float)prm->G; a.e = (float)prm->e_incr; a.scale = (float)prm->energy_scale;
+    a.w_weight = (float)prm->w_weight;
     a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t0; a.n_incr = n_incr; a.P = st->P;
     a.eps_p = st->eps_p; a.gamma = st->gamma; a.g = st->g;
     a.sigma = sigma; a.w = w; a.erho = erho; a.b = b;

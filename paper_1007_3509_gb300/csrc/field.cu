@@ -113,8 +113,10 @@ __global__ void k_bins(int32_t G, int32_t kind, const float* orient, int32_t* bi
     const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
     const double pi = 3.14159265358979323846;
-    if (kind == HP_ORIENT_ANGLE) {
-        const double deg = (double)orient[g] * (180.0 / pi);
+    if (kind == HP_ORIENT_ANGLE || kind == HP_ORIENT_ZROT) {
+        const double t = kind == HP_ORIENT_ANGLE ? (double)orient[g]
+                                                 : 2.0 * atan2((double)orient[4 * g + 3], (double)orient[4 * g]);
+        const double deg = t * (180.0 / pi);
         int b = (int)floor(deg);
         bins[g] = b < 0 ? 0 : (b > 89 ? 89 : b);
         return;
@@ -144,7 +146,7 @@ __global__ void k_hist(int32_t G, int32_t kind, const int32_t* bins, const unsig
     if (g >= G) return;
     const unsigned long long c = counts[g];
     if (!c) return;
-    if (kind == HP_ORIENT_ANGLE) {
+    if (kind != HP_ORIENT_SO3) {
         atomicAdd(hist + bins[g], c);
     } else {
         atomicAdd(hist + bins[2 * g], c);
@@ -152,10 +154,32 @@ __global__ void k_hist(int32_t G, int32_t kind, const int32_t* bins, const unsig
     }
 }
 
+// Orientation-dependent Gaussian bulk energy of Eq. (9): the grain's angle
+// selects orientation n = floor(angle in degrees) + 1 (1..90) and
+// b(n) = (32 pi)^(-1/2) exp(-(n - 46)^2 / (2 * 46^2)) [J], quantised.
+__global__ void k_gaussian_field(int32_t G, const float* angle, double scale, int32_t* b) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const double pi = 3.14159265358979323846;
+    int bin = (int)floor((double)angle[g] * (180.0 / pi));
+    bin = bin < 0 ? 0 : (bin > 89 ? 89 : bin);
+    const double n = bin + 1.0;
+    const double e = scale * exp(-(n - 46.0) * (n - 46.0) / (2.0 * 46.0 * 46.0)) / sqrt(32.0 * pi);
+    b[g] = (int32_t)rint(256.0 * e);
+}
+
 }  // namespace
 }  // namespace hp
 
 using namespace hp;
+
+extern "C" int hp_gaussian_field(int32_t G, const float* angle, double scale, int32_t* b_out, void* stream) {
+    if (G < 1 || !angle || !b_out || !(fabs(scale) < 1e3)) return set_error(HP_ERR_ARG, "hp_gaussian_field: bad arguments");
+    ::hp::count_launch();
+    k_gaussian_field<<<(G + kT - 1) / kT, kT, 0, as_stream(stream)>>>(G, angle, scale, b_out);
+    HP_LAUNCH_CHECK("k_gaussian_field");
+    return HP_OK;
+}
 
 extern "C" int hp_grain_field(int32_t G, const float* quat, double C11, double C12, double C44, double sigma,
                               double k_disl, double energy_scale, int32_t* b_out, float* w_out, float* mmax_out,
@@ -210,13 +234,13 @@ extern "C" int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, vo
 
 extern "C" int hp_texture(int32_t G, int32_t orient_kind, const float* orient, const int64_t* counts, int32_t* bins,
                           int64_t* hist, void* stream) {
-    if (G < 1 || !orient || !bins || (orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_SO3))
+    if (G < 1 || !orient || !bins || orient_kind < HP_ORIENT_ANGLE || orient_kind > HP_ORIENT_ZROT)
         return set_error(HP_ERR_ARG, "hp_texture: bad arguments");
     cudaStream_t s = as_stream(stream);
     ::hp::count_launch();
     k_bins<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, orient, bins);
     if (hist && counts) {
-        const int nb = orient_kind == HP_ORIENT_ANGLE ? 90 : 24;
+        const int nb = orient_kind == HP_ORIENT_SO3 ? 24 : 90;
         HP_CUDA(cudaMemsetAsync(hist, 0, sizeof(int64_t) * nb, s));
         ::hp::count_launch();
         k_hist<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, bins,

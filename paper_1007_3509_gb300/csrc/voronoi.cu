@@ -161,6 +161,14 @@ __global__ void k_orient(int32_t G, uint64_t seed, int32_t kind, float* out) {
     const double two32 = 4294967296.0, pi = 3.14159265358979323846;
     if (kind == HP_ORIENT_ANGLE) {
         out[g] = (float)(((double)u.x / two32) * (pi / 2.0));
+    } else if (kind == HP_ORIENT_ZROT) {
+        const double t = ((double)u.x / two32) * (pi / 2.0);
+        double sh, ch;
+        sincos(0.5 * t, &sh, &ch);
+        out[4 * g + 0] = (float)ch;
+        out[4 * g + 1] = 0.0f;
+        out[4 * g + 2] = 0.0f;
+        out[4 * g + 3] = (float)sh;
     } else {
         const double u1 = (double)u.x / two32, u2 = (double)u.y / two32, u3 = (double)u.z / two32;
         const double a = sqrt(1.0 - u1), b = sqrt(u1);
@@ -177,7 +185,7 @@ __global__ void k_orient(int32_t G, uint64_t seed, int32_t kind, float* out) {
 }  // namespace
 
 int orientations_run(int32_t G, uint64_t seed, int32_t kind, float* orient, cudaStream_t s) {
-    if (G < 1 || !orient || (kind != HP_ORIENT_ANGLE && kind != HP_ORIENT_SO3))
+    if (G < 1 || !orient || kind < HP_ORIENT_ANGLE || kind > HP_ORIENT_ZROT)
         return set_error(HP_ERR_ARG, "hp_orientations: bad arguments");
     ::hp::count_launch();
     k_orient<<<(G + kT - 1) / kT, kT, 0, s>>>(G, seed, kind, orient);
@@ -315,7 +323,7 @@ extern "C" int hp_init_voronoi_static(hp_handle* h, int32_t orient_kind, float* 
     using namespace hp;
     if (!h) return set_error(HP_ERR_ARG, "hp_init_voronoi_static: null handle");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_init_voronoi_static: no lattice bound");
-    if (orient && orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_SO3)
+    if (orient && (orient_kind < HP_ORIENT_ANGLE || orient_kind > HP_ORIENT_ZROT))
         return set_error(HP_ERR_ARG, "hp_init_voronoi_static: bad orient_kind");
     const int32_t G = h->desc.n_grains;
     const int64_t N = h->lat.N;

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhmcpotts.so")
 
 HP_OK, HP_ERR_ARG, HP_ERR_CUDA, HP_ERR_OOM, HP_ERR_TIMEOUT, HP_ERR_STATE, HP_ERR_CHECKSUM = 0, -1, -2, -3, -4, -5, -6
 FIELD_NONE, FIELD_GRAIN, FIELD_POINT = 0, 1, 2
-ORIENT_ANGLE, ORIENT_SO3 = 0, 1
+ORIENT_ANGLE, ORIENT_SO3, ORIENT_ZROT = 0, 1, 2
 SWEEP_AUTO, SWEEP_PHASE, SWEEP_FUSED = 0, 1, 2
 
 _lock = threading.Lock()
@@ -39,7 +39,7 @@ class hp_desc(C.Structure):
 class hp_cp_params(C.Structure):
     _fields_ = [("C11", C.c_double), ("C12", C.c_double), ("C44", C.c_double), ("tau0", C.c_double),
                 ("taus", C.c_double), ("h0", C.c_double), ("beta", C.c_double), ("G", C.c_double),
-                ("e_incr", C.c_double), ("energy_scale", C.c_double)]
+                ("e_incr", C.c_double), ("energy_scale", C.c_double), ("w_weight", C.c_double)]
 
 
 class hp_sur_scales(C.Structure):
@@ -80,6 +80,7 @@ _SIGS = {
     "hp_texture": ([C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_grain_field": ([C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                         C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_gaussian_field": ([C.c_int32, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p], C.c_int),
     "hp_texture_fit": ([C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     "hp_checkpoint_save": ([C.c_void_p, C.c_char_p, C.c_void_p], C.c_int),
     "hp_checkpoint_load": ([C.c_void_p, C.c_char_p, C.c_void_p], C.c_int),
@@ -178,6 +179,10 @@ def hp_texture(G, kind, orient, counts, bins, hist, stream=None):
                             _stream(stream)))
 
 
+def hp_gaussian_field(G, angle, scale, b_out, stream=None):
+    _check(lib().hp_gaussian_field(int(G), _ptr(angle), float(scale), _ptr(b_out), _stream(stream)))
+
+
 def hp_texture_fit(hist):
     """Fit g (degrees) of Eq. (10) to a 90-bin angle histogram (host numpy int64)."""
     h = np.ascontiguousarray(hist, dtype=np.int64)
@@ -231,10 +236,10 @@ def hp_sur_field(params, quat, G, load, energy_scale, b_out, e_out=None, scales=
                               float(energy_scale), _ptr(b_out), _ptr(e_out), _stream(stream)))
 
 
-def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=None):
+def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=None, w_weight=1.0):
     if G is None:
         G = (C11 - C12 + 3.0 * C44) / 5.0
-    return hp_cp_params(C11, C12, C44, tau0, taus, h0, beta, G, e_incr, energy_scale)
+    return hp_cp_params(C11, C12, C44, tau0, taus, h0, beta, G, e_incr, energy_scale, w_weight)
 
 
 def hp_cp_reset(prm, P, eps_p, gamma, g, stream=None):

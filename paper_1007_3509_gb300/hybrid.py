@@ -36,10 +36,10 @@ class HybridConfig:
     energy_scale: float = 7.0  # J per MJ/m^3: population maximum of b near 0.1 J
 
 
-def cp_params_table1(e_incr, energy_scale):
+def cp_params_table1(e_incr, energy_scale, w_weight=1.0):
     c = synth.TABLE1
     return hm.cp_params(c["C11"], c["C12"], c["C44"], c["tau0"], c["taus"], c["h0"], c["beta"], e_incr,
-                        energy_scale=energy_scale)
+                        energy_scale=energy_scale, w_weight=w_weight)
 
 
 def _texture(torch, lat, quat, G):

@@ -60,7 +60,7 @@ def test_voronoi_full_size_sampled(oracle, dim, L, G, seed):
     del q
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_orientations_match(oracle, kind):
     torch, hm = need_gpu()
     G = 100_000
@@ -106,11 +106,11 @@ def test_counts_and_texture_match(oracle):
     ref_c, ref_alive = oracle.grain_counts(q0, G)
     np.testing.assert_array_equal(counts.cpu().numpy(), ref_c)
     assert int(alive.item()) == ref_alive
-    for kind in (0, 1):
+    for kind in (0, 1, 2):
         orient = oracle.orientations(G, 55, kind)
         to = torch.from_numpy(np.ascontiguousarray(orient)).cuda()
-        bins = torch.empty(G * (1 if kind == 0 else 2), dtype=torch.int32, device="cuda")
-        hist = torch.empty(90 if kind == 0 else 24, dtype=torch.int64, device="cuda")
+        bins = torch.empty(G * (2 if kind == 1 else 1), dtype=torch.int32, device="cuda")
+        hist = torch.empty(24 if kind == 1 else 90, dtype=torch.int64, device="cuda")
         hm.hp_texture(G, kind, to, counts, bins, hist)
         rb, near = oracle.grain_bins(orient, kind)
         gb = bins.cpu().numpy().reshape(rb.shape)

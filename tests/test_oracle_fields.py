@@ -66,6 +66,18 @@ def test_quaternion_rotation_matches_scipy(oracle):
         np.testing.assert_allclose(oracle.loading_axis(q), R.T @ np.array([1.0, 0, 0]), atol=1e-6)
 
 
+def test_zrot_quaternion_is_angle_about_z(oracle):
+    """Kind 2 is the rotation by the kind-0 angle about z (scipy rotation vector (0, 0, t))."""
+    a = oracle.orientations(200, 17, 0).astype(np.float64)
+    q = oracle.orientations(200, 17, 2)
+    ref = Rotation.from_rotvec(np.stack([np.zeros_like(a), np.zeros_like(a), a], 1)).as_quat()  # x,y,z,w
+    np.testing.assert_allclose(q, np.stack([ref[:, 3], ref[:, 0], ref[:, 1], ref[:, 2]], 1), atol=1e-7)
+    bins, near = oracle.grain_bins(q, 2)
+    b0, _ = oracle.grain_bins(a.astype(np.float32), 0)
+    ok = near > 1e-6
+    np.testing.assert_array_equal(bins[ok], b0[ok])
+
+
 def test_orientations_uniform_on_so3(oracle):
     """Shoemake quaternions: rotation angle has CDF (t - sin t)/pi; the loading axis is uniform on the sphere."""
     q = oracle.orientations(20000, 31, 1).astype(np.float64)
@@ -178,6 +190,17 @@ def test_grain_field_uniaxial_energy(oracle):
     assert abs(w[0] - 0.03668) < 5e-5
     assert abs(mm[0] - 1 / math.sqrt(6)) < 1e-7
     assert b[0] == int(np.rint(256 * (w[0] + 0.05 * mm[0])))
+
+
+def test_gaussian_bulk_energy_eq9(oracle):
+    """Eq. (9): symmetric about n = 46 with peak (32 pi)^(-1/2); orientation n = floor(degrees) + 1."""
+    deg = np.arange(90) + 0.5
+    e, b = oracle.gaussian_field(np.radians(deg).astype(np.float32))
+    assert abs(e[45] - 1 / math.sqrt(32 * math.pi)) < 1e-15 and np.argmax(e) == 45
+    for k in range(1, 45):   # e(46 - k) == e(46 + k)
+        assert abs(e[45 - k] - e[45 + k]) < 1e-15
+    assert abs(e[0] - math.exp(-45 ** 2 / (2 * 46 ** 2)) / math.sqrt(32 * math.pi)) < 1e-15
+    np.testing.assert_array_equal(b, np.rint(256 * e).astype(np.int32))
 
 
 def test_quantise_round_half_even(oracle):
