@@ -55,7 +55,7 @@ def parse():
     a = p.parse_args()
     if a.mcs is None:
         a.mcs = {"2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20, "texture2d": 1000,
-                 "texture3d": 100}[a.workload]
+                 "texture3d": 400}[a.workload]
     return a
 
 
@@ -631,9 +631,11 @@ def run_texture(args):
                           "seconds": round(r["seconds"], 2),
                           "site_updates_per_s": round(100 * 500 * 500 * args.mcs / r["seconds"], 1)}))
     else:
-        r = texture.run_plastic_3d(torch, L=(256, 256, 256), G=30000, kT=2.6, n_incr=args.mcs, mcs_per_incr=1,
-                                   e_incr=2e-5, energy_scale=50.0, every=max(1, args.mcs // 10))
-        print(json.dumps({"workload": "texture3d-plastic-zrot-256^3", "t": r["t"],
+        n_incr = max(1, args.mcs // 2)
+        r = texture.run_plastic_3d(torch, L=(256, 256, 256), G=32000, kT=1.0, n_incr=n_incr, mcs_per_incr=2,
+                                   e_incr=1e-4, energy_scale=200.0, every=max(1, n_incr // 10))
+        print(json.dumps({"workload": "texture3d-plastic-zrot-256^3", "grains": 32000, "kT": 1.0,
+                          "e_incr": 1e-4, "energy_scale": 200.0, "mcs": 2 * n_incr, "t": r["t"],
                           "g_deg": [round(x, 3) for x in r["g"]], "seconds": round(r["seconds"], 2)}))
 
 

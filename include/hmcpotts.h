@@ -333,7 +333,8 @@ typedef struct {
  * increments t = 1..n_incr (Eq. (3)) in K stochastic histories (K material
  * points, Philox counters n_orient*K apart).  After increment t, with
  * sigma_hat(t) = population average of the sample-frame stress R sigma R^T and
- * gamma_hat(t) = average slip, sample (t-1)*n_orient + o is
+ * gamma_hat(t) = average slip, sample o*n_incr + (t-1) is (orientation-major,
+ * so any contiguous run of rows covers whole orientations at every increment)
  *   X = (f(q_o), sigma_hat(t)/stress, gamma_hat(t)/strain)     (device float[.][11])
  * where f(q) encodes the orientation by four cubic invariants of the loading
  * axis d = R(q)^T e_x: |d| sorted in decreasing order and

@@ -31,8 +31,9 @@ def orientation_features(quat):
 
 
 def samples(P, seed, quat, K, n_incr, scales):
-    """Returns X [n_incr*n_orient, 11], Y [n_incr*n_orient, 2], load [n_incr, 7],
-    and a per-orientation near-tie flag (any history within 1e-5 of a decision)."""
+    """Returns X [n_orient*n_incr, 11], Y [n_orient*n_incr, 2] (row o*n_incr + t-1),
+    load [n_incr, 7], and a per-orientation near-tie flag (any history within
+    1e-5 of a decision)."""
     quat = np.ascontiguousarray(quat, dtype=np.float32)
     n_orient = quat.shape[0]
     grain = np.repeat(np.arange(n_orient, dtype=np.int32), K)
@@ -63,4 +64,6 @@ def samples(P, seed, quat, K, n_incr, scales):
         y = np.stack([w.reshape(n_orient, K).mean(1) / scales[2], er.reshape(n_orient, K).mean(1) / scales[3]], axis=1)
         X.append(x)
         Y.append(y)
-    return np.concatenate(X), np.concatenate(Y), np.array(load), near
+    X = np.stack(X, axis=1).reshape(n_orient * n_incr, 11)
+    Y = np.stack(Y, axis=1).reshape(n_orient * n_incr, 2)
+    return X, Y, np.array(load), near

@@ -94,9 +94,12 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
     return {"wall_s": wall, "field_s": t_field, **tex}
 
 
-def train_surrogate(torch, prm, n_orient=16384, K=32, n_incr=20, steps=20000, lr=3e-3, seed=3000, log_every=0):
-    """Generate samples with the MCP kernel and fit the network with the tensor-core kernels.
-    Returns (params tensor, load table [n_incr, 7] (numpy), final loss, history)."""
+def train_surrogate(torch, prm, n_orient=16384, K=32, n_incr=20, steps=20000, lr=3e-3, seed=3000, log_every=0,
+                    batch=32768):
+    """Generate samples with the MCP kernel and fit the network with the tensor-core kernels,
+    Adam on contiguous minibatches of `batch` rows taken in turn (rows are orientation-major,
+    so each minibatch holds whole orientations at every increment; batch=None uses all rows).
+    Returns (params tensor, load table [n_incr, 7] (numpy), final minibatch loss, history)."""
     quat = torch.empty(n_orient, 4, dtype=torch.float32, device="cuda")
     hm.hp_orientations(n_orient, seed, hm.ORIENT_SO3, quat)
     M = n_orient * n_incr
@@ -112,9 +115,12 @@ def train_surrogate(torch, prm, n_orient=16384, K=32, n_incr=20, steps=20000, lr
     v = torch.zeros(n, device="cuda")
     loss = torch.zeros(1, device="cuda")
     hist = []
+    B = M if batch is None else min(int(batch) // n_incr * n_incr, M)
+    n_batches = max(1, M // B)
     for step in range(1, steps + 1):
         lr_t = lr * (0.02 + 0.98 * 0.5 * (1 + np.cos(np.pi * step / steps)))  # cosine decay
-        hm.hp_mlp_gradients(params, X, Y, grads, loss)
+        r0 = ((step - 1) % n_batches) * B
+        hm.hp_mlp_gradients(params, X[r0:r0 + B], Y[r0:r0 + B], grads, loss)
         hm.hp_mlp_adam(params, grads, m, v, step, lr_t)
         if log_every and step % log_every == 0:
             hist.append((step, float(loss.item())))

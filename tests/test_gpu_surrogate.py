@@ -34,7 +34,7 @@ def test_generate_matches_oracle():
     P = oracle.cp_params(c["C11"], c["C12"], c["C44"], c["tau0"], c["taus"], c["h0"], c["beta"], 1e-4)
     Xr, Yr, Lr, near = osur.samples(P, seed, quat, K, n_incr, SC)
     assert near.mean() < 0.1
-    ok = np.tile(~near, n_incr)
+    ok = np.repeat(~near, n_incr)
     np.testing.assert_allclose(Y.cpu().numpy()[ok], Yr[ok], rtol=2e-4, atol=1e-6)
     tol = 1e-4 if not near.any() else 5e-3
     np.testing.assert_allclose(load.cpu().numpy(), Lr, rtol=tol, atol=1e-4)
