@@ -170,6 +170,20 @@ class Job:
         self.measure()
 
 
+def sweep_kernel_name(nbr, variant):
+    """Kernel family of a fused-sweep tile variant (variant numbering of hp_sweep_variants)."""
+    v = int(variant or 0)
+    plane_n = 6 if nbr == 26 else 5
+    strip_end = 9
+    if v < plane_n:
+        kind = "k_plane_tma" if (v >= plane_n - 2) else "k_plane"
+    elif v < strip_end:
+        kind = "k_strip"
+    else:
+        kind = "k_tile"
+    return f"{kind}<{nbr}> (fused MCS, variant {v})"
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1007_3509_gb300 import build, hmcpotts as hm
@@ -216,7 +230,8 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-            "kernel": "k_plane<8> (fused 4-colour MCS)", "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
+            "kernel": sweep_kernel_name(W.nbr, job.tuned.get("variant") if job.tuned else 0),
+            "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
             "sweep_site_updates_per_s": round(job.N / per_launch_s, 1)}
     traffic = os.environ.get("HP_SWEEP_TRAFFIC_BYTES")
     if traffic:

@@ -24,77 +24,12 @@
 
 #include <cudaTypedefs.h>
 
-#include "common.cuh"
+#include "sweep.cuh"
 
 namespace hp {
 namespace {
 
 constexpr int kThreads = 256;
-
-template <int DIM, int NBR>
-struct Geo;
-
-// 2D-4: +x, -x, +y, -y ; colours (x+y)&1
-template <>
-struct Geo<2, 4> {
-    static constexpr int M = 4, C = 2;
-    __device__ static void off(int k, int& dx, int& dy, int& dz) {
-        dx = k == 0 ? 1 : (k == 1 ? -1 : 0);
-        dy = k == 2 ? 1 : (k == 3 ? -1 : 0);
-        dz = 0;
-    }
-};
-// 2D-8: (dy,dx) row-major without (0,0) ; colours (x&1) + 2(y&1)
-template <>
-struct Geo<2, 8> {
-    static constexpr int M = 8, C = 4;
-    __device__ static void off(int k, int& dx, int& dy, int& dz) {
-        const int kk = k + (k >= 4);
-        dy = kk / 3 - 1;
-        dx = kk % 3 - 1;
-        dz = 0;
-    }
-};
-// 3D-6: +x, -x, +y, -y, +z, -z ; colours (x+y+z)&1
-template <>
-struct Geo<3, 6> {
-    static constexpr int M = 6, C = 2;
-    __device__ static void off(int k, int& dx, int& dy, int& dz) {
-        dx = k == 0 ? 1 : (k == 1 ? -1 : 0);
-        dy = k == 2 ? 1 : (k == 3 ? -1 : 0);
-        dz = k == 4 ? 1 : (k == 5 ? -1 : 0);
-    }
-};
-// 3D-26: (dz,dy,dx) lexicographic without (0,0,0) ; colours (x&1)+2(y&1)+4(z&1)
-template <>
-struct Geo<3, 26> {
-    static constexpr int M = 26, C = 8;
-    __device__ static void off(int k, int& dx, int& dy, int& dz) {
-        const int kk = k + (k >= 13);
-        dz = kk / 9 - 1;
-        dy = (kk / 3) % 3 - 1;
-        dx = kk % 3 - 1;
-    }
-};
-
-__device__ __forceinline__ int wrapi(int a, int L) {
-    a %= L;
-    return a < 0 ? a + L : a;
-}
-
-__device__ __forceinline__ bool metropolis(int32_t d, int32_t D, const uint32_t* __restrict__ thr, uint32_t u) {
-    if (d < 0) return true;
-    if (d > D) return false;
-    const uint32_t t = __ldg(thr + d);
-    return t == 0xFFFFFFFFu || u < t;
-}
-
-// Field-table lookup with the index clamped into the table (ids come from
-// caller buffers; an out-of-range id must not read outside the table).
-__device__ __forceinline__ int32_t tab(const int32_t* __restrict__ t, uint32_t n, int32_t i) {
-    const uint32_t u = (uint32_t)i;
-    return __ldg(t + (u < n ? u : n - 1));
-}
 
 struct PhaseArgs {
     int32_t* q;
@@ -195,32 +130,6 @@ __global__ void __launch_bounds__(kThreads) k_phase(PhaseArgs a) {
 // every lane of every warp busy.  The order inside a phase is irrelevant: no
 // two sites of one colour are neighbours.
 // ---------------------------------------------------------------------------
-struct PlaneArgs {
-    const int32_t* q_in;    // own plane, previous state
-    const int32_t* mp_in;
-    const int32_t* q_nb;    // z-neighbour planes (3D)
-    const int32_t* mp_nb;
-    int32_t* q_out;
-    int32_t* mp_out;
-    const int32_t* table;
-    uint32_t table_n;
-    const uint32_t* thr;
-    int32_t D, J;
-    uint64_t seed;
-    uint32_t sweep;
-    int Lx, Ly, Lz;
-    int zpar;               // 3D: parity of the planes handled by this launch
-    int tiles_x;
-    int tiles;              // tiles per plane
-    int fast;               // 1: window narrower than the lattice (wrap by one add)
-    int vec;                // 1: fast and Lx % 4 == 0 (16-byte row chunks)
-};
-
-__device__ __forceinline__ int wrap1(int a, int L) {
-    a += a < 0 ? L : 0;
-    return a - (a >= L ? L : 0);
-}
-
 template <int NBR, int WX_, int TY>
 struct PlaneCfg {
     static constexpr int H = 4;
@@ -401,6 +310,20 @@ __device__ __forceinline__ void plane_body(const PlaneArgs& a, const int tile, c
             const int32_t* pj = dz == 0 ? s_q : (dz < 0 ? s_lo : s_hi);
             const int32_t qj = pj[cj];
             if (qj == qi) continue;
+            // the material point and field loads go out first; their latency
+            // overlaps the neighbour count
+            int32_t mpj = 0;
+            if (HASMP) {
+                if (dz == 0) {
+                    mpj = s_mp[cj];
+                } else {
+                    const int jx = wrap1(gx + dx, a.Lx), jy = wrap1(gy + dy, a.Ly);
+                    mpj = __ldg(a.mp_nb + jx + (int64_t)a.Lx * jy + sxy * (dz < 0 ? zlo : zhi));
+                }
+            }
+            int32_t bi = 0, bj = 0;
+            if (FIELD == 1) { bi = tab(a.table, a.table_n, qi); bj = tab(a.table, a.table_n, qj); }
+            if (FIELD == 2) { bi = tab(a.table, a.table_n, s_mp[c0]); bj = tab(a.table, a.table_n, mpj); }
             int same_new;
             if (NBR == 4) {
                 same_new = (s_q[cl] == qj) + (s_q[cr] == qj) + (s_q[c0 - WXH] == qj) + (s_q[c0 + WXH] == qj);
@@ -416,20 +339,7 @@ __device__ __forceinline__ void plane_body(const PlaneArgs& a, const int tile, c
                     }
                 }
             }
-            int32_t mpj = 0;
-            if (HASMP) {
-                if (dz == 0) {
-                    mpj = s_mp[cj];
-                } else {
-                    const int jx = wrapi(gx + dx, a.Lx), jy = wrapi(gy + dy, a.Ly);
-                    const int jz = dz < 0 ? zlo : zhi;
-                    mpj = a.mp_nb[jx + (int64_t)a.Lx * jy + sxy * jz];
-                }
-            }
-            int32_t db = 0;
-            if (FIELD == 1) db = tab(a.table, a.table_n, qj) - tab(a.table, a.table_n, qi);
-            if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, s_mp[c0]);
-            const int32_t d = a.J * (same_old - same_new) + db;
+            const int32_t d = a.J * (same_old - same_new) + (bj - bi);
             if (metropolis(d, a.D, a.thr, u.y)) {
                 s_q[c0] = qj;
                 if (HASMP) s_mp[c0] = mpj;
@@ -537,7 +447,6 @@ struct TmaCfg {
     static constexpr size_t smem() { return 2 * STAGE + sizeof(uint32_t) * QCAP + 64 + 1024; }
 };
 
-__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int rank,
                                          uint32_t mbar) {
@@ -550,19 +459,6 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
             ::"r"(dst), "l"(m), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-        if (clock64() - t0 > (1ll << 32)) return false;
-    }
 }
 
 // wrap-aware manual load of a row-major window (edge items)
@@ -763,6 +659,18 @@ __global__ void __launch_bounds__(kThreads, 4)
                 const int32_t* pj = dz == 0 ? s_q : (dz < 0 ? s_lo : s_hi);
                 const int32_t qj = pj[lj];
                 if (qj == qi) continue;
+                int32_t mpj = 0;
+                if (HASMP) {
+                    if (dz == 0) {
+                        mpj = s_mp[lj];
+                    } else {
+                        const int jx = wrap1(gx + dx, a.Lx), jy = wrap1(gy + dy, a.Ly);
+                        mpj = __ldg(a.mp_nb + jx + (int64_t)a.Lx * jy + sxy * (dz < 0 ? zlo : zhi));
+                    }
+                }
+                int32_t bi = 0, bj = 0;
+                if (FIELD == 1) { bi = tab(a.table, a.table_n, qi); bj = tab(a.table, a.table_n, qj); }
+                if (FIELD == 2) { bi = tab(a.table, a.table_n, s_mp[li]); bj = tab(a.table, a.table_n, mpj); }
                 int same_new = 0;
                 if (NBR == 4) {
                     same_new = (s_q[li - 1] == qj) + (s_q[li + 1] == qj) + (s_q[li - WX] == qj) + (s_q[li + WX] == qj);
@@ -776,19 +684,7 @@ __global__ void __launch_bounds__(kThreads, 4)
                             if (Z) same_new += (s_lo[o] == qj) + (s_hi[o] == qj);
                         }
                 }
-                int32_t mpj = 0;
-                if (HASMP) {
-                    if (dz == 0) {
-                        mpj = s_mp[lj];
-                    } else {
-                        const int jx = wrapi(gx + dx, a.Lx), jy = wrapi(gy + dy, a.Ly);
-                        mpj = a.mp_nb[jx + (int64_t)a.Lx * jy + sxy * (dz < 0 ? zlo : zhi)];
-                    }
-                }
-                int32_t db = 0;
-                if (FIELD == 1) db = tab(a.table, a.table_n, qj) - tab(a.table, a.table_n, qi);
-                if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, s_mp[li]);
-                const int32_t d = a.J * (same_old - same_new) + db;
+                const int32_t d = a.J * (same_old - same_new) + (bj - bi);
                 if (metropolis(d, a.D, a.thr, u.y)) {
                     s_q[li] = qj;
                     if (HASMP) s_mp[li] = mpj;
@@ -885,15 +781,26 @@ int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
 // core height TY, plain (parity-split window, one CTA per item) or TMA-fed
 // (row-major window, persistent CTAs).  All give identical lattices; the
 // autotuner picks one.  TMA variants serve single lattices only.
+// Strip variants (strip.cu): one warp per strip, WX = 32 x columns per lane,
+// TY = most core rows per strip.  Tile variants (tile.cu): WX x (TY + 8)
+// windows fed by bulk TMA copies.
 struct Variant {
     int WX, TY;
     bool tma;
+    bool strip;
+    bool tile;
 };
-constexpr int kVariants2D = 5, kVariants3D = 6;
-constexpr Variant kV2D[kVariants2D] = {{128, 64, false}, {128, 32, false}, {64, 64, false}, {128, 32, true},
-                                       {128, 24, true}};
-constexpr Variant kV3D[kVariants3D] = {{128, 32, false}, {128, 16, false}, {64, 32, false}, {64, 16, false},
-                                       {64, 32, true}, {64, 16, true}};
+constexpr int kVariants2D = 12, kVariants3D = 12;
+constexpr Variant kV2D[kVariants2D] = {
+    {128, 64, false, false, false}, {128, 32, false, false, false}, {64, 64, false, false, false},
+    {128, 32, true, false, false},  {128, 24, true, false, false},  {256, 16, false, true, false},
+    {256, 32, false, true, false},  {128, 16, false, true, false},  {128, 32, false, true, false},
+    {128, 24, false, false, true},  {128, 56, false, false, true},  {64, 56, false, false, true}};
+constexpr Variant kV3D[kVariants3D] = {
+    {128, 32, false, false, false}, {128, 16, false, false, false}, {64, 32, false, false, false},
+    {64, 16, false, false, false},  {64, 32, true, false, false},   {64, 16, true, false, false},
+    {64, 64, false, true, false},   {128, 64, false, true, false},  {64, 32, false, true, false},
+    {64, 56, false, false, true},   {64, 24, false, false, true},   {128, 24, false, false, true}};
 
 int n_variants(int nbr) { return nbr == 26 ? kVariants3D : (nbr == 6 ? 1 : kVariants2D); }
 Variant variant_of(int nbr, int v) { return nbr == 26 ? kV3D[v] : kV2D[v]; }
@@ -1003,6 +910,17 @@ int launch_fm_tma(int field, bool m, const PlaneArgs* a, int planes, cudaStream_
 
 int launch_variant(int nbr, int v, int field, bool m, const PlaneArgs* a, const BatchArgs* b, int64_t blocks,
                    int planes, cudaStream_t s) {
+    const Variant var = variant_of(nbr, v);
+    if (var.tile) {
+        if (!a) return set_error(HP_ERR_ARG, "sweep: tile variants serve single lattices only");
+        if (blocks == 0) return HP_OK;
+        return tile_launch(*a, field, m, nbr, planes, var.WX, var.TY + 8, s);
+    }
+    if (var.strip) {
+        if (!a) return set_error(HP_ERR_ARG, "sweep: strip variants serve single lattices only");
+        if (blocks == 0) return HP_OK;
+        return strip_launch(*a, field, m, nbr, planes, var.WX / 32, var.TY, s);
+    }
     if (nbr == 4) {
         switch (v) {
             case 0: return launch_fm<4, 128, 64, true>(field, m, a, b, blocks, planes, s);
@@ -1037,7 +955,8 @@ bool variant_ok(int nbr, int v, int field, bool m) {
 }
 
 bool variant_batch_ok(int nbr, int v, int field, bool m) {
-    return variant_ok(nbr, v, field, m) && !variant_of(nbr, v).tma;
+    const Variant var = variant_of(nbr, v);
+    return variant_ok(nbr, v, field, m) && !var.tma && !var.strip && !var.tile;
 }
 
 // Arguments of the fused kernel for one lattice and one launch.
@@ -1319,13 +1238,15 @@ extern "C" int hp_set_sweep_variant(hp_handle* h, int32_t v) {
 
 extern "C" int hp_sweep_status(int32_t* timed_out) {
     if (!timed_out) return set_error(HP_ERR_ARG, "hp_sweep_status: null argument");
-    int v = 0, zero = 0;
+    int v = 0, vs = 0, zero = 0;
     HP_CUDA(cudaMemcpyFromSymbol(&v, g_sweep_err, sizeof(int)));
-    *timed_out = v;
-    if (v) {
-        HP_CUDA(cudaMemcpyToSymbol(g_sweep_err, &zero, sizeof(int)));
-        return set_error(HP_ERR_TIMEOUT, "sweep: a TMA copy did not complete in time");
-    }
+    if (v) HP_CUDA(cudaMemcpyToSymbol(g_sweep_err, &zero, sizeof(int)));
+    int vt = 0;
+    int rc = strip_status(&vs);
+    if (!rc) rc = tile_status(&vt);
+    if (rc) return rc;
+    *timed_out = (v || vs || vt) ? 1 : 0;
+    if (*timed_out) return set_error(HP_ERR_TIMEOUT, "sweep: a TMA copy did not complete in time");
     return HP_OK;
 }
 

@@ -1,0 +1,375 @@
+// Tile kernel: the fused checkerboard sweep (Eq. (7), Sec. 4) on a row-major
+// window in shared memory, built to spend few instructions per site.
+//
+// One CTA = one WX x WY window (a halo of four sites around a (WX-8) x (WY-8)
+// core) of one plane.  The window's rows arrive by bulk TMA copies
+// (cp.async.bulk, one per row and array, a second one where a row crosses the
+// periodic x boundary; completion on one mbarrier with a clock-limited wait).
+// All colour phases that live in the plane then run in shared memory; in 3D
+// the planes z-1 and z+1 are read-only neighbours (old for even planes, new for
+// odd planes), exactly as in the plane kernel, and each MCS is two launches.
+//
+// Per phase:
+//   A. every thread takes one aligned quad of four columns in one row of the
+//      colour: one 128-bit and one 32-bit shared load per neighbour row give the
+//      two sites of the colour in the quad and all their neighbours; a site is
+//      interior when the OR of (neighbour XOR site) over its neighbourhood is
+//      zero.  The other sites go to a block-wide queue, one atomic per warp.
+//   B. every queued site draws Philox and picks its neighbour (each thread
+//      takes two queue entries at once, so their Philox rounds overlap); the
+//      proposals of another grain are compacted into a per-warp queue, and the
+//      warp then counts both grains among each one's neighbours and runs the
+//      Metropolis test with all lanes busy.
+// Columns and rows outside [p+1, W-p-1) are left alone in phase p; after the
+// last phase the core is exact and is written to the output buffer.
+#include "sweep.cuh"
+
+namespace hp {
+namespace {
+
+constexpr int kTileThreads = 256;
+__device__ int g_tile_err;
+
+template <int NBR, int WX, int WY, bool HASMP>
+struct TileCfg {
+    static constexpr bool Z = NBR == 26;
+    static constexpr int H = 4, TX = WX - 2 * H, TY = WY - 2 * H;
+    static constexpr int ARR = 1 + (HASMP ? 1 : 0) + (Z ? 2 : 0);  // q, mp, q(z-1), q(z+1)
+    static constexpr int A_MP = 1, A_LO = HASMP ? 2 : 1, A_HI = A_LO + 1;
+    static constexpr int NP = NBR == 4 ? 2 : 4;
+    static constexpr int PAD = 8;                  // ints of padding before and after each array
+    static constexpr int AS = WX * WY + 2 * PAD;   // array stride in ints
+    static constexpr int QPR = WX / 4;             // quads per row
+    static constexpr int RPP = kTileThreads / QPR; // rows per pass of stage A
+    static constexpr int QCAP = NBR == 4 ? (WX / 2) * WY : (WX / 2) * ((WY + 1) / 2);
+    static_assert(WX % 4 == 0 && (AS * 4) % 16 == 0 && kTileThreads % QPR == 0, "tile shape");
+    static size_t smem() { return 128 + sizeof(int32_t) * ((size_t)ARR * AS + QCAP + 8) + sizeof(uint2) * 64 * (kTileThreads / 32); }
+};
+
+template <int NBR, int WX, int WY, int FIELD, bool HASMP>
+struct Tile {
+    using Cfg = TileCfg<NBR, WX, WY, HASMP>;
+    static constexpr int M = NBR;
+    const PlaneArgs& a;
+    int32_t* S;      // q of the plane
+    int32_t* SMP;    // mp of the plane
+    int32_t* SLO;    // q of plane z-1
+    int32_t* SHI;    // q of plane z+1
+    int x0, y0, z, zlo, zhi;
+    int64_t sxy;
+    bool fast;
+
+    __device__ Tile(const PlaneArgs& a_) : a(a_) {}
+
+    __device__ __forceinline__ int gx_of(int col) const {
+        return fast ? wrap1(x0 - 4 + col, a.Lx) : wrapi(x0 - 4 + col, a.Lx);
+    }
+    __device__ __forceinline__ int gy_of(int r) const {
+        return fast ? wrap1(y0 - 4 + r, a.Ly) : wrapi(y0 - 4 + r, a.Ly);
+    }
+    __device__ __forceinline__ static void offs(int kp, int& dx, int& dy, int& dz) {
+        if (NBR == 4) Geo<2, 4>::off(kp, dx, dy, dz);
+        else if (NBR == 8) Geo<2, 8>::off(kp, dx, dy, dz);
+        else Geo<3, 26>::off(kp, dx, dy, dz);
+    }
+
+    // Draw for the queued site e = (row << 8) | col; true when the proposed
+    // neighbour carries another grain (then w = (pos | k << 16, u1) goes on).
+    __device__ __forceinline__ bool draw_site(uint32_t e, uint32_t colour, uint2& w) const {
+        const int r = (int)(e >> 8), col = (int)(e & 255u);
+        const int pos = r * WX + col;
+        const uint4 u = draw(a.seed, (uint64_t)(gx_of(col) + (int64_t)a.Lx * gy_of(r) + sxy * z), a.sweep, kTagSweep,
+                             colour);
+        const int kp = (int)__umulhi(u.x, (uint32_t)M);
+        int dx, dy, dz;
+        offs(kp, dx, dy, dz);
+        const int32_t qj = (dz == 0 ? S : (dz < 0 ? SLO : SHI))[pos + dy * WX + dx];
+        w = make_uint2((uint32_t)pos | ((uint32_t)kp << 16), u.y);
+        return qj != S[pos];
+    }
+
+    // Metropolis test of a proposal that changes the site's grain.
+    __device__ __forceinline__ void test(uint2 w) const {
+        const int pos = (int)(w.x & 0xFFFFu), kp = (int)(w.x >> 16);
+        int dx, dy, dz;
+        offs(kp, dx, dy, dz);
+        const int off = dy * WX + dx;
+        const int32_t qi = S[pos];
+        const int32_t qj = (dz == 0 ? S : (dz < 0 ? SLO : SHI))[pos + off];
+        int32_t mpj = 0, bi = 0, bj = 0;
+        if (HASMP) {
+            if (dz == 0) {
+                mpj = SMP[pos + off];
+            } else {
+                const int r = pos / WX, col = pos - r * WX;
+                mpj = __ldg(a.mp_nb + wrap1(gx_of(col) + dx, a.Lx) + (int64_t)a.Lx * wrap1(gy_of(r) + dy, a.Ly) +
+                            sxy * (dz < 0 ? zlo : zhi));
+            }
+        }
+        if (FIELD == 1) { bi = tab(a.table, a.table_n, qi); bj = tab(a.table, a.table_n, qj); }
+        if (FIELD == 2) { bi = tab(a.table, a.table_n, SMP[pos]); bj = tab(a.table, a.table_n, mpj); }
+        int so = 0, sn = 0;
+        auto cnt = [&](int32_t v) { so += v == qi; sn += v == qj; };
+        const int32_t* c = S + pos;
+        if (NBR == 4) {
+            cnt(c[-1]); cnt(c[1]); cnt(c[-WX]); cnt(c[WX]);
+        } else {
+#pragma unroll
+            for (int ddy = -1; ddy <= 1; ++ddy)
+#pragma unroll
+                for (int ddx = -1; ddx <= 1; ++ddx)
+                    if (ddx || ddy) cnt(c[ddy * WX + ddx]);
+            if (Cfg::Z) {
+                const int32_t* l = SLO + pos;
+                const int32_t* h = SHI + pos;
+#pragma unroll
+                for (int ddy = -1; ddy <= 1; ++ddy)
+#pragma unroll
+                    for (int ddx = -1; ddx <= 1; ++ddx) {
+                        cnt(l[ddy * WX + ddx]);
+                        cnt(h[ddy * WX + ddx]);
+                    }
+            }
+        }
+        const int32_t d = a.J * (so - sn) + (bj - bi);
+        if (metropolis(d, a.D, a.thr, w.y)) {
+            S[pos] = qj;
+            if (HASMP) SMP[pos] = mpj;
+        }
+    }
+};
+
+template <int NBR, int WX, int WY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const __grid_constant__ PlaneArgs a, int tma) {
+    using T = Tile<NBR, WX, WY, FIELD, HASMP>;
+    using Cfg = typename T::Cfg;
+    constexpr int ARR = Cfg::ARR, AS = Cfg::AS, PAD = Cfg::PAD, NP = Cfg::NP, QPR = Cfg::QPR, RPP = Cfg::RPP;
+    constexpr int M = NBR;
+    constexpr bool Z = Cfg::Z;
+    extern __shared__ __align__(16) unsigned char raw[];
+    int32_t* base = reinterpret_cast<int32_t*>(raw + ((128u - (s_addr(raw) & 127u)) & 127u));
+    uint32_t* queue = reinterpret_cast<uint32_t*>(base + ARR * AS);
+    int* qn = reinterpret_cast<int*>(queue + Cfg::QCAP);                       // 4 counters
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(qn + 4);  // 8-byte aligned
+    uint2* wqueue = reinterpret_cast<uint2*>(qn + 8);                          // 64 per warp
+
+    T t(a);
+    t.S = base + PAD;
+    t.SMP = base + (HASMP ? AS + PAD : PAD);
+    t.SLO = base + Cfg::A_LO * AS + PAD;
+    t.SHI = base + Cfg::A_HI * AS + PAD;
+    const int tile = blockIdx.x;
+    const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+    t.x0 = tx * Cfg::TX;
+    t.y0 = ty * Cfg::TY;
+    t.z = Z ? 2 * (int)blockIdx.y + a.zpar : 0;
+    t.zlo = Z ? wrapi(t.z - 1, a.Lz) : 0;
+    t.zhi = Z ? wrapi(t.z + 1, a.Lz) : 0;
+    t.sxy = (int64_t)a.Lx * a.Ly;
+    t.fast = a.fast != 0;
+    const int64_t sxy = t.sxy;
+
+    auto src = [&](int arr) -> const int32_t* {
+        if (arr == 0) return a.q_in + sxy * t.z;
+        if (HASMP && arr == Cfg::A_MP) return a.mp_in + sxy * t.z;
+        return a.q_nb + sxy * (arr == Cfg::A_LO ? t.zlo : t.zhi);
+    };
+    if (threadIdx.x < 4) qn[threadIdx.x] = 0;
+    bool ok = true;
+    if (tma) {
+        const uint32_t mb = s_addr(mbar);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                             "r"((uint32_t)(ARR * WY * WX * 4)) : "memory");
+            __syncwarp();
+            for (int i = threadIdx.x; i < ARR * WY; i += 32) {
+                const int arr = i / WY, r = i - arr * WY;
+                copy_row(base + arr * AS + PAD + r * WX, src(arr) + (int64_t)a.Lx * t.gy_of(r), t.x0 - 4, WX, a.Lx, mb);
+            }
+        }
+        ok = wait_parity(mb, 0u);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(&g_tile_err, 1);
+                wait_parity(mb, 0u);  // the copies in flight land before the block leaves (bounded)
+            }
+            return;
+        }
+    } else {
+        for (int i = threadIdx.x; i < ARR * WY * WX; i += kTileThreads) {
+            const int arr = i / (WY * WX), rem = i - arr * (WY * WX), r = rem / WX, c = rem - r * WX;
+            base[arr * AS + PAD + rem] = src(arr)[(int64_t)a.Lx * wrapi(t.y0 - 4 + r, a.Ly) + wrapi(t.x0 - 4 + c, a.Lx)];
+        }
+        __syncthreads();
+    }
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int qd = threadIdx.x % QPR, rs = threadIdx.x / QPR;
+    const int c0 = 4 * qd;
+    const uint32_t cz = Z ? 4u * (uint32_t)a.zpar : 0u;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int lo = p + 1, hi = WX - p - 1, hiy = WY - p - 1;
+        // ---- A: interior test, queue the rest ---------------------------------
+        constexpr int RSTEP = NBR == 4 ? 1 : 2;
+        const int rstart = NBR == 4 ? lo : lo + ((lo ^ (p >> 1)) & 1);
+        for (int r0 = rstart; r0 < hiy; r0 += RSTEP * RPP) {
+            const int r = r0 + RSTEP * rs;
+            const int px = NBR == 4 ? ((r + p) & 1) : (p & 1);
+            const int ca = c0 + px, cb = ca + 2;
+            const bool va = r < hiy && ca >= lo && ca < hi;
+            const bool vb = r < hiy && cb >= lo && cb < hi;
+            uint32_t acc0 = 0, acc1 = 0;
+            if (va || vb) {
+                const int rowq = r * WX + c0;
+                const int32_t* own = t.S + rowq;
+                const int4 cv = *reinterpret_cast<const int4*>(own);
+                const int32_t q0 = px ? cv.y : cv.x, q1 = px ? cv.w : cv.z;
+                // the three columns around each site in one row of plane P
+                auto row = [&](const int32_t* P, bool centre) {
+                    const int4 v = *reinterpret_cast<const int4*>(P);
+                    const int32_t e = px ? P[4] : P[-1];
+                    const int32_t l0 = px ? v.x : e, m0 = px ? v.y : v.x, r0_ = px ? v.z : v.y;
+                    const int32_t l1 = px ? v.z : v.y, m1 = px ? v.w : v.z, r1 = px ? e : v.w;
+                    acc0 |= (l0 ^ q0) | (r0_ ^ q0);
+                    acc1 |= (l1 ^ q1) | (r1 ^ q1);
+                    if (!centre) { acc0 |= m0 ^ q0; acc1 |= m1 ^ q1; }
+                };
+                if (NBR == 4) {
+                    row(own, true);
+                    acc0 |= ((px ? own[1 - WX] : own[-WX]) ^ q0) | ((px ? own[1 + WX] : own[WX]) ^ q0);
+                    acc1 |= ((px ? own[3 - WX] : own[2 - WX]) ^ q1) | ((px ? own[3 + WX] : own[2 + WX]) ^ q1);
+                } else {
+                    row(own - WX, false);
+                    row(own, true);
+                    row(own + WX, false);
+                    if (Z) {
+#pragma unroll
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            row(t.SLO + rowq + dy * WX, false);
+                            row(t.SHI + rowq + dy * WX, false);
+                        }
+                    }
+                }
+            }
+            const bool ba = va && acc0 != 0u, bb = vb && acc1 != 0u;
+            const unsigned ma = __ballot_sync(0xFFFFFFFFu, ba), mbb = __ballot_sync(0xFFFFFFFFu, bb);
+            if (ma | mbb) {
+                int k = 0;
+                if (lane == 0) k = atomicAdd(qn + p, __popc(ma) + __popc(mbb));
+                k = __shfl_sync(0xFFFFFFFFu, k, 0);
+                if (ba) queue[k + __popc(ma & lt)] = ((uint32_t)r << 8) | (uint32_t)ca;
+                if (bb) queue[k + __popc(ma) + __popc(mbb & lt)] = ((uint32_t)r << 8) | (uint32_t)cb;
+            }
+        }
+        __syncthreads();
+        // ---- B: Metropolis update of the queued sites, two per thread --------
+        const uint32_t colour = NBR == 4 ? (uint32_t)p : cz + (uint32_t)p;
+        // B1: each thread draws for two queued sites; the proposals of another
+        // grain go to its warp's queue.  B2: the warp tests them, all lanes busy.
+        const int n = qn[p];
+        uint2* wq = wqueue + 64 * (threadIdx.x >> 5);
+        for (int k0 = 0; k0 < n; k0 += 2 * kTileThreads) {
+            const int k1 = k0 + (int)threadIdx.x, k2 = k1 + kTileThreads;
+            uint2 w1 = make_uint2(0u, 0u), w2 = make_uint2(0u, 0u);
+            const bool a1 = k1 < n && t.draw_site(queue[k1], colour, w1);
+            const bool a2 = k2 < n && t.draw_site(queue[k2], colour, w2);
+            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
+            if (a1) wq[__popc(m1 & lt)] = w1;
+            if (a2) wq[__popc(m1) + __popc(m2 & lt)] = w2;
+            __syncwarp();
+            const int na = __popc(m1) + __popc(m2);
+            for (int j = lane; j < na; j += 32) t.test(wq[j]);
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    (void)M;
+
+    // ---- write the core: rows [4, WY - 4), quads 1 .. QPR - 2 ----------------
+    int32_t* qo = a.q_out + sxy * t.z;
+    int32_t* mpo = HASMP ? a.mp_out + sxy * t.z : nullptr;
+    constexpr int CQ = QPR - 2;
+    for (int i = threadIdx.x; i < Cfg::TY * CQ; i += kTileThreads) {
+        const int cy = i / CQ, qq = 1 + (i - cy * CQ);
+        const int gx = t.x0 + 4 * (qq - 1), gy = t.y0 + cy;
+        if (gx >= a.Lx || gy >= a.Ly) continue;
+        const int li = (cy + 4) * WX + 4 * qq;
+        const int64_t o = gx + (int64_t)a.Lx * gy;
+        if (a.vec) {
+            *reinterpret_cast<int4*>(qo + o) = *reinterpret_cast<const int4*>(t.S + li);
+            if (HASMP) *reinterpret_cast<int4*>(mpo + o) = *reinterpret_cast<const int4*>(t.SMP + li);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (gx + j >= a.Lx) break;
+                qo[o + j] = t.S[li + j];
+                if (HASMP) mpo[o + j] = t.SMP[li + j];
+            }
+        }
+    }
+}
+
+template <int NBR, int WX, int WY, int FIELD, bool HASMP>
+int launch_tile(const PlaneArgs& a, int tma, int planes, cudaStream_t s) {
+    using Cfg = TileCfg<NBR, WX, WY, HASMP>;
+    auto fn = k_tile<NBR, WX, WY, FIELD, HASMP>;
+    const size_t smem = Cfg::smem();
+    static bool configured = false;
+    if (!configured) {
+        HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    if (a.tiles == 0) return HP_OK;
+    count_launch();
+    fn<<<dim3((unsigned)a.tiles, (unsigned)planes), kTileThreads, smem, s>>>(a, tma);
+    HP_LAUNCH_CHECK("k_tile");
+    return HP_OK;
+}
+
+template <int NBR, int WX, int WY>
+int tile_fm(const PlaneArgs& a, int tma, int field, bool m, int planes, cudaStream_t s) {
+    if (field == HP_FIELD_GRAIN && !m) return launch_tile<NBR, WX, WY, 1, false>(a, tma, planes, s);
+    if (field == HP_FIELD_POINT) return launch_tile<NBR, WX, WY, 2, true>(a, tma, planes, s);
+    return set_error(HP_ERR_ARG, "sweep: tile variant not built for this field mode");
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+int tile_launch(const PlaneArgs& a, int field, bool hasmp, int nbr, int planes, int WX, int WY, cudaStream_t s) {
+    const bool ptr_ok = al16(a.q_in) && (!hasmp || al16(a.mp_in)) && (nbr != 26 || al16(a.q_nb));
+    const int tma = (a.Lx % 4 == 0 && WX <= a.Lx && ptr_ok) ? 1 : 0;
+    if (nbr == 8) {
+        if (WX == 128 && WY == 32) return tile_fm<8, 128, 32>(a, tma, field, hasmp, planes, s);
+        if (WX == 128 && WY == 64) return tile_fm<8, 128, 64>(a, tma, field, hasmp, planes, s);
+        if (WX == 64 && WY == 64) return tile_fm<8, 64, 64>(a, tma, field, hasmp, planes, s);
+    } else if (nbr == 4) {
+        if (WX == 128 && WY == 32) return tile_fm<4, 128, 32>(a, tma, field, hasmp, planes, s);
+        if (WX == 128 && WY == 64) return tile_fm<4, 128, 64>(a, tma, field, hasmp, planes, s);
+        if (WX == 64 && WY == 64) return tile_fm<4, 64, 64>(a, tma, field, hasmp, planes, s);
+    } else if (nbr == 26) {
+        if (WX == 64 && WY == 64) return tile_fm<26, 64, 64>(a, tma, field, hasmp, planes, s);
+        if (WX == 64 && WY == 32) return tile_fm<26, 64, 32>(a, tma, field, hasmp, planes, s);
+        if (WX == 128 && WY == 32) return tile_fm<26, 128, 32>(a, tma, field, hasmp, planes, s);
+    }
+    return set_error(HP_ERR_ARG, "sweep: no tile kernel of this shape");
+}
+
+int tile_status(int* timed_out) {
+    int v = 0, zero = 0;
+    HP_CUDA(cudaMemcpyFromSymbol(&v, g_tile_err, sizeof(int)));
+    if (v) HP_CUDA(cudaMemcpyToSymbol(g_tile_err, &zero, sizeof(int)));
+    *timed_out = v;
+    return HP_OK;
+}
+
+}  // namespace hp
