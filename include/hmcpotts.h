@@ -160,8 +160,8 @@ HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
 /* Tile variants of the fused sweep kernel: plane tiles (window width x core
  * height, plain or TMA-fed persistent), warp strips (one warp walks a strip of
  * one plane, rows streamed by bulk TMA copies) and lean tiles (row-major
- * windows filled by bulk TMA copies).  All give identical lattices; only the
- * plain plane tiles serve ensembles.  Variants 0-4 (2D) / 0-5 (3D) are plane
+ * windows filled by bulk TMA copies).  All give identical lattices; ensembles take
+ * the plain plane tiles and the lean tiles.  Variants 0-4 (2D) / 0-5 (3D) are plane
  * tiles, 5-8 (2D) / 6-8 (3D) strips, 9-11 lean tiles.
  * hp_sweep_variants: how many exist for `nbr`.
  * hp_set_sweep_variant: choose one (HP_ERR_ARG if not built for the handle's

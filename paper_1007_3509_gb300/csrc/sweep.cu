@@ -912,9 +912,8 @@ int launch_variant(int nbr, int v, int field, bool m, const PlaneArgs* a, const 
                    int planes, cudaStream_t s) {
     const Variant var = variant_of(nbr, v);
     if (var.tile) {
-        if (!a) return set_error(HP_ERR_ARG, "sweep: tile variants serve single lattices only");
-        if (blocks == 0) return HP_OK;
-        return tile_launch(*a, field, m, nbr, planes, var.WX, var.TY + 8, s);
+        if (a) return blocks == 0 ? HP_OK : tile_launch(*a, field, m, nbr, planes, var.WX, var.TY + 8, s);
+        return tile_launch_batch(b->args, b->start, b->R, blocks, b->sweep_add, field, m, nbr, var.WX, var.TY + 8, s);
     }
     if (var.strip) {
         if (!a) return set_error(HP_ERR_ARG, "sweep: strip variants serve single lattices only");
@@ -956,7 +955,7 @@ bool variant_ok(int nbr, int v, int field, bool m) {
 
 bool variant_batch_ok(int nbr, int v, int field, bool m) {
     const Variant var = variant_of(nbr, v);
-    return variant_ok(nbr, v, field, m) && !var.tma && !var.strip && !var.tile;
+    return variant_ok(nbr, v, field, m) && !var.tma && !var.strip;
 }
 
 // Arguments of the fused kernel for one lattice and one launch.

@@ -145,6 +145,10 @@ __device__ __forceinline__ void copy_row(int32_t* dst, const int32_t* row, int x
 // Tile kernel (tile.cu): one launch over the planes of one parity; WX x WY
 // window (core (WX - 8) x (WY - 8)), a.tiles_x / a.tiles set for that core.
 int tile_launch(const PlaneArgs& a, int field, bool hasmp, int nbr, int planes, int WX, int WY, cudaStream_t s);
+// The same over many lattices: d_args[R] (device), block offsets d_start[R+1];
+// blocks == 0 only configures the kernel (outside a graph capture).
+int tile_launch_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, int64_t blocks, uint32_t sweep_add,
+                      int field, bool hasmp, int nbr, int WX, int WY, cudaStream_t s);
 // Reads and clears the tile kernel's timeout flag.
 int tile_status(int* timed_out);
 

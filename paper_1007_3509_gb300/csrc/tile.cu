@@ -139,14 +139,18 @@ struct Tile {
     }
 };
 
+__device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 template <int NBR, int WX, int WY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const __grid_constant__ PlaneArgs a, int tma) {
+__device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, const int zidx, unsigned char* raw) {
     using T = Tile<NBR, WX, WY, FIELD, HASMP>;
     using Cfg = typename T::Cfg;
     constexpr int ARR = Cfg::ARR, AS = Cfg::AS, PAD = Cfg::PAD, NP = Cfg::NP, QPR = Cfg::QPR, RPP = Cfg::RPP;
     constexpr int M = NBR;
     constexpr bool Z = Cfg::Z;
-    extern __shared__ __align__(16) unsigned char raw[];
+    // rows by bulk TMA copies when a row of the window wraps at most once and
+    // every source row starts on a 16-byte boundary
+    const bool tma = a.Lx % 4 == 0 && WX <= a.Lx && al16(a.q_in) && (!HASMP || al16(a.mp_in)) && (!Z || al16(a.q_nb));
     int32_t* base = reinterpret_cast<int32_t*>(raw + ((128u - (s_addr(raw) & 127u)) & 127u));
     uint32_t* queue = reinterpret_cast<uint32_t*>(base + ARR * AS);
     int* qn = reinterpret_cast<int*>(queue + Cfg::QCAP);                       // 4 counters
@@ -158,11 +162,10 @@ __global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const 
     t.SMP = base + (HASMP ? AS + PAD : PAD);
     t.SLO = base + Cfg::A_LO * AS + PAD;
     t.SHI = base + Cfg::A_HI * AS + PAD;
-    const int tile = blockIdx.x;
     const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
     t.x0 = tx * Cfg::TX;
     t.y0 = ty * Cfg::TY;
-    t.z = Z ? 2 * (int)blockIdx.y + a.zpar : 0;
+    t.z = Z ? 2 * zidx + a.zpar : 0;
     t.zlo = Z ? wrapi(t.z - 1, a.Lz) : 0;
     t.zhi = Z ? wrapi(t.z + 1, a.Lz) : 0;
     t.sxy = (int64_t)a.Lx * a.Ly;
@@ -318,50 +321,105 @@ __global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const 
 }
 
 template <int NBR, int WX, int WY, int FIELD, bool HASMP>
-int launch_tile(const PlaneArgs& a, int tma, int planes, cudaStream_t s) {
+__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const __grid_constant__ PlaneArgs a) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    tile_body<NBR, WX, WY, FIELD, HASMP>(a, (int)blockIdx.x, (int)blockIdx.y, raw);
+}
+
+// Many independent lattices in one launch: block b belongs to the replica r
+// with start[r] <= b < start[r+1]; within it b - start[r] = zidx * tiles + tile.
+template <int NBR, int WX, int WY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4)
+    k_tile_batch(const PlaneArgs* __restrict__ args, const int64_t* __restrict__ start, int R, uint32_t sweep_add) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    __shared__ PlaneArgs sa;
+    __shared__ int s_tile, s_zidx;
+    if (threadIdx.x == 0) {
+        const int64_t blk = blockIdx.x;
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= blk) lo = mid; else hi = mid - 1;
+        }
+        sa = args[lo];
+        sa.sweep += sweep_add;
+        const int64_t local = blk - start[lo];
+        s_zidx = (int)(local / sa.tiles);
+        s_tile = (int)(local - (int64_t)s_zidx * sa.tiles);
+    }
+    __syncthreads();
+    tile_body<NBR, WX, WY, FIELD, HASMP>(sa, s_tile, s_zidx, raw);
+}
+
+struct TileBatch {
+    const PlaneArgs* args;
+    const int64_t* start;
+    int R;
+    int64_t blocks;
+    uint32_t sweep_add;
+};
+
+template <int NBR, int WX, int WY, int FIELD, bool HASMP>
+int launch_tile(const PlaneArgs* a, const TileBatch* b, int planes, cudaStream_t s) {
     using Cfg = TileCfg<NBR, WX, WY, HASMP>;
-    auto fn = k_tile<NBR, WX, WY, FIELD, HASMP>;
     const size_t smem = Cfg::smem();
     static bool configured = false;
     if (!configured) {
-        HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HP_CUDA(cudaFuncSetAttribute(k_tile<NBR, WX, WY, FIELD, HASMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        HP_CUDA(cudaFuncSetAttribute(k_tile_batch<NBR, WX, WY, FIELD, HASMP>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    if (a.tiles == 0) return HP_OK;
-    count_launch();
-    fn<<<dim3((unsigned)a.tiles, (unsigned)planes), kTileThreads, smem, s>>>(a, tma);
+    if (a) {
+        if (a->tiles == 0) return HP_OK;
+        count_launch();
+        k_tile<NBR, WX, WY, FIELD, HASMP><<<dim3((unsigned)a->tiles, (unsigned)planes), kTileThreads, smem, s>>>(*a);
+    } else {
+        if (b->blocks == 0) return HP_OK;  // configure only
+        count_launch();
+        k_tile_batch<NBR, WX, WY, FIELD, HASMP><<<(unsigned)b->blocks, kTileThreads, smem, s>>>(b->args, b->start, b->R,
+                                                                                                 b->sweep_add);
+    }
     HP_LAUNCH_CHECK("k_tile");
     return HP_OK;
 }
 
 template <int NBR, int WX, int WY>
-int tile_fm(const PlaneArgs& a, int tma, int field, bool m, int planes, cudaStream_t s) {
-    if (field == HP_FIELD_GRAIN && !m) return launch_tile<NBR, WX, WY, 1, false>(a, tma, planes, s);
-    if (field == HP_FIELD_POINT) return launch_tile<NBR, WX, WY, 2, true>(a, tma, planes, s);
+int tile_fm(const PlaneArgs* a, const TileBatch* b, int field, bool m, int planes, cudaStream_t s) {
+    if (field == HP_FIELD_GRAIN && !m) return launch_tile<NBR, WX, WY, 1, false>(a, b, planes, s);
+    if (field == HP_FIELD_POINT) return launch_tile<NBR, WX, WY, 2, true>(a, b, planes, s);
     return set_error(HP_ERR_ARG, "sweep: tile variant not built for this field mode");
 }
 
-bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+int tile_dispatch(const PlaneArgs* a, const TileBatch* b, int field, bool hasmp, int nbr, int planes, int WX, int WY,
+                  cudaStream_t s) {
+    if (nbr == 8) {
+        if (WX == 128 && WY == 32) return tile_fm<8, 128, 32>(a, b, field, hasmp, planes, s);
+        if (WX == 128 && WY == 64) return tile_fm<8, 128, 64>(a, b, field, hasmp, planes, s);
+        if (WX == 64 && WY == 64) return tile_fm<8, 64, 64>(a, b, field, hasmp, planes, s);
+    } else if (nbr == 4) {
+        if (WX == 128 && WY == 32) return tile_fm<4, 128, 32>(a, b, field, hasmp, planes, s);
+        if (WX == 128 && WY == 64) return tile_fm<4, 128, 64>(a, b, field, hasmp, planes, s);
+        if (WX == 64 && WY == 64) return tile_fm<4, 64, 64>(a, b, field, hasmp, planes, s);
+    } else if (nbr == 26) {
+        if (WX == 64 && WY == 64) return tile_fm<26, 64, 64>(a, b, field, hasmp, planes, s);
+        if (WX == 64 && WY == 32) return tile_fm<26, 64, 32>(a, b, field, hasmp, planes, s);
+        if (WX == 128 && WY == 32) return tile_fm<26, 128, 32>(a, b, field, hasmp, planes, s);
+    }
+    return set_error(HP_ERR_ARG, "sweep: no tile kernel of this shape");
+}
 
 }  // namespace
 
 int tile_launch(const PlaneArgs& a, int field, bool hasmp, int nbr, int planes, int WX, int WY, cudaStream_t s) {
-    const bool ptr_ok = al16(a.q_in) && (!hasmp || al16(a.mp_in)) && (nbr != 26 || al16(a.q_nb));
-    const int tma = (a.Lx % 4 == 0 && WX <= a.Lx && ptr_ok) ? 1 : 0;
-    if (nbr == 8) {
-        if (WX == 128 && WY == 32) return tile_fm<8, 128, 32>(a, tma, field, hasmp, planes, s);
-        if (WX == 128 && WY == 64) return tile_fm<8, 128, 64>(a, tma, field, hasmp, planes, s);
-        if (WX == 64 && WY == 64) return tile_fm<8, 64, 64>(a, tma, field, hasmp, planes, s);
-    } else if (nbr == 4) {
-        if (WX == 128 && WY == 32) return tile_fm<4, 128, 32>(a, tma, field, hasmp, planes, s);
-        if (WX == 128 && WY == 64) return tile_fm<4, 128, 64>(a, tma, field, hasmp, planes, s);
-        if (WX == 64 && WY == 64) return tile_fm<4, 64, 64>(a, tma, field, hasmp, planes, s);
-    } else if (nbr == 26) {
-        if (WX == 64 && WY == 64) return tile_fm<26, 64, 64>(a, tma, field, hasmp, planes, s);
-        if (WX == 64 && WY == 32) return tile_fm<26, 64, 32>(a, tma, field, hasmp, planes, s);
-        if (WX == 128 && WY == 32) return tile_fm<26, 128, 32>(a, tma, field, hasmp, planes, s);
-    }
-    return set_error(HP_ERR_ARG, "sweep: no tile kernel of this shape");
+    return tile_dispatch(&a, nullptr, field, hasmp, nbr, planes, WX, WY, s);
+}
+
+int tile_launch_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, int64_t blocks, uint32_t sweep_add,
+                      int field, bool hasmp, int nbr, int WX, int WY, cudaStream_t s) {
+    TileBatch b{d_args, d_start, R, blocks, sweep_add};
+    return tile_dispatch(nullptr, &b, field, hasmp, nbr, 1, WX, WY, s);
 }
 
 int tile_status(int* timed_out) {

@@ -119,3 +119,41 @@ def test_ensemble_rejects_mixed_members():
     b, _ = _member(torch, hm, 2, (8, 8), 8, 1, 0.7, "grain")
     with pytest.raises(hm.HPError):
         hm.Ensemble([a, b])
+
+
+@pytest.mark.parametrize("kind", ["3d", "2d"])
+@pytest.mark.parametrize("mode", ["grain", "point"])
+def test_ensemble_every_batch_variant_bit_exact(oracle, kind, mode):
+    """Every tile variant that ensembles accept (plane and lean tiles), replayed twice."""
+    torch, hm = need_gpu()
+    dim, nbr = (3, 26) if kind == "3d" else (2, 8)
+    geoms = ENS[kind][:3]
+    tried = 0
+    for v in range(hm.hp_sweep_variants(nbr)):
+        members, refs = [], []
+        for r, (L, kT) in enumerate(geoms):
+            lat, ref = _member(torch, hm, dim, L, nbr, 3000 + r, kT, mode, G=25 + 5 * r, rs=10 + r)
+            members.append(lat)
+            refs.append(ref)
+        ens = hm.Ensemble(members)
+        try:
+            ens.hp_ensemble_set_variant(v)
+        except hm.HPError:
+            ens.close()
+            for lat in members:
+                lat.close()
+            continue
+        tried += 1
+        ens.hp_ensemble_sweep(2)
+        ens.hp_ensemble_sweep(2)
+        torch.cuda.synchronize()
+        for lat, ref in zip(members, refs):
+            rq, rmp = _oracle_run(oracle, ref, 4)
+            q, mp, _ = lat._bufs
+            np.testing.assert_array_equal(q.cpu().numpy(), rq, err_msg=f"{ref['L']} variant {v}")
+            if mode == "point":
+                np.testing.assert_array_equal(mp.cpu().numpy(), rmp, err_msg=f"{ref['L']} variant {v}")
+        ens.close()
+        for lat in members:
+            lat.close()
+    assert tried >= 4
