@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-secondary", action="store_true")
     p.add_argument("--mcs", type=int, default=None, help="MCS per step (default: the workload's)")
-    p.add_argument("--variant", type=int, default=None, help="sweep3d: tile variant (default: autotuned)")
+    p.add_argument("--variant", type=int, default=None, help="fused-sweep tile variant (default: autotuned)")
     p.add_argument("--workload", choices=["2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
                                           "texture3d"], default="2d",
                    help="2d: 4096^2 Moore (default line); 3d-cp: 512^3 plasticity-driven hybrid; ensemble: 256 "
@@ -194,7 +194,10 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     hm.lib()
     job = Job(torch, hm, W.seed + rank, args.mcs)
-    if not args.no_autotune:
+    if args.variant is not None:
+        job.lat.hp_set_sweep_variant(args.variant)
+        job.tuned = {"variant": int(args.variant), "ms_per_8_mcs": None}
+    elif not args.no_autotune:
         job.autotune()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     for _ in range(args.warmup):

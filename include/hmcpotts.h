@@ -162,7 +162,7 @@ HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
  * one plane, rows streamed by bulk TMA copies) and lean tiles (row-major
  * windows filled by bulk TMA copies).  All give identical lattices; ensembles take
  * the plain plane tiles and the lean tiles.  Variants 0-4 (2D) / 0-5 (3D) are plane
- * tiles, 5-8 (2D) / 6-8 (3D) strips, 9-11 lean tiles.
+ * tiles, 5-8 (2D) / 6-8 (3D) strips, 9-11 (and 12 in 3D) lean tiles.
  * hp_sweep_variants: how many exist for `nbr`.
  * hp_set_sweep_variant: choose one (HP_ERR_ARG if not built for the handle's
  * field mode).  hp_sweep_autotune: time every variant for n_mcs MCS on a

@@ -790,7 +790,7 @@ struct Variant {
     bool strip;
     bool tile;
 };
-constexpr int kVariants2D = 12, kVariants3D = 12;
+constexpr int kVariants2D = 12, kVariants3D = 13;
 constexpr Variant kV2D[kVariants2D] = {
     {128, 64, false, false, false}, {128, 32, false, false, false}, {64, 64, false, false, false},
     {128, 32, true, false, false},  {128, 24, true, false, false},  {256, 16, false, true, false},
@@ -800,7 +800,8 @@ constexpr Variant kV3D[kVariants3D] = {
     {128, 32, false, false, false}, {128, 16, false, false, false}, {64, 32, false, false, false},
     {64, 16, false, false, false},  {64, 32, true, false, false},   {64, 16, true, false, false},
     {64, 64, false, true, false},   {128, 64, false, true, false},  {64, 32, false, true, false},
-    {64, 56, false, false, true},   {64, 24, false, false, true},   {128, 24, false, false, true}};
+    {64, 56, false, false, true},   {64, 24, false, false, true},   {128, 24, false, false, true},
+    {64, 32, false, false, true}};
 
 int n_variants(int nbr) { return nbr == 26 ? kVariants3D : (nbr == 6 ? 1 : kVariants2D); }
 Variant variant_of(int nbr, int v) { return nbr == 26 ? kV3D[v] : kV2D[v]; }

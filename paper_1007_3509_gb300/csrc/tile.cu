@@ -227,38 +227,44 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
             const int r = r0 + RSTEP * rs;
             const int px = NBR == 4 ? ((r + p) & 1) : (p & 1);
             const int ca = c0 + px, cb = ca + 2;
-            const bool va = r < hiy && ca >= lo && ca < hi;
-            const bool vb = r < hiy && cb >= lo && cb < hi;
+            const bool rowok = r < hiy;
+            const bool va = rowok && ca >= lo && ca < hi;
+            const bool vb = rowok && cb >= lo && cb < hi;
+            // every lane loads (lanes past the last row read row hiy - 1 and
+            // discard it) so that the edge columns can come from the
+            // neighbouring lanes: the left lane's last column and the right
+            // lane's first.  A lane at the end of a warp row only ever holds a
+            // site outside [lo, hi) on that side.
+            const int rowq = (rowok ? r : hiy - 1) * WX + c0;
+            const int32_t* own = t.S + rowq;
+            const int4 cv = *reinterpret_cast<const int4*>(own);
+            const int32_t q0 = px ? cv.y : cv.x, q1 = px ? cv.w : cv.z;
             uint32_t acc0 = 0, acc1 = 0;
-            if (va || vb) {
-                const int rowq = r * WX + c0;
-                const int32_t* own = t.S + rowq;
-                const int4 cv = *reinterpret_cast<const int4*>(own);
-                const int32_t q0 = px ? cv.y : cv.x, q1 = px ? cv.w : cv.z;
-                // the three columns around each site in one row of plane P
-                auto row = [&](const int32_t* P, bool centre) {
-                    const int4 v = *reinterpret_cast<const int4*>(P);
-                    const int32_t e = px ? P[4] : P[-1];
-                    const int32_t l0 = px ? v.x : e, m0 = px ? v.y : v.x, r0_ = px ? v.z : v.y;
-                    const int32_t l1 = px ? v.z : v.y, m1 = px ? v.w : v.z, r1 = px ? e : v.w;
-                    acc0 |= (l0 ^ q0) | (r0_ ^ q0);
-                    acc1 |= (l1 ^ q1) | (r1 ^ q1);
-                    if (!centre) { acc0 |= m0 ^ q0; acc1 |= m1 ^ q1; }
-                };
-                if (NBR == 4) {
-                    row(own, true);
-                    acc0 |= ((px ? own[1 - WX] : own[-WX]) ^ q0) | ((px ? own[1 + WX] : own[WX]) ^ q0);
-                    acc1 |= ((px ? own[3 - WX] : own[2 - WX]) ^ q1) | ((px ? own[3 + WX] : own[2 + WX]) ^ q1);
-                } else {
-                    row(own - WX, false);
-                    row(own, true);
-                    row(own + WX, false);
-                    if (Z) {
+            // the three columns around each site in one row (values v)
+            auto cols = [&](const int4 v, bool centre) {
+                const int32_t el = __shfl_up_sync(0xFFFFFFFFu, v.w, 1);
+                const int32_t er = __shfl_down_sync(0xFFFFFFFFu, v.x, 1);
+                const int32_t l0 = px ? v.x : el, m0 = px ? v.y : v.x, r0_ = px ? v.z : v.y;
+                const int32_t l1 = px ? v.z : v.y, m1 = px ? v.w : v.z, r1 = px ? er : v.w;
+                acc0 |= (l0 ^ q0) | (r0_ ^ q0);
+                acc1 |= (l1 ^ q1) | (r1 ^ q1);
+                if (!centre) { acc0 |= m0 ^ q0; acc1 |= m1 ^ q1; }
+            };
+            auto ld = [&](const int32_t* P) { return *reinterpret_cast<const int4*>(P); };
+            if (NBR == 4) {
+                cols(cv, true);
+                const int4 u = ld(own - WX), d = ld(own + WX);
+                acc0 |= ((px ? u.y : u.x) ^ q0) | ((px ? d.y : d.x) ^ q0);
+                acc1 |= ((px ? u.w : u.z) ^ q1) | ((px ? d.w : d.z) ^ q1);
+            } else {
+                cols(ld(own - WX), false);
+                cols(cv, true);
+                cols(ld(own + WX), false);
+                if (Z) {
 #pragma unroll
-                        for (int dy = -1; dy <= 1; ++dy) {
-                            row(t.SLO + rowq + dy * WX, false);
-                            row(t.SHI + rowq + dy * WX, false);
-                        }
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        cols(ld(t.SLO + rowq + dy * WX), false);
+                        cols(ld(t.SHI + rowq + dy * WX), false);
                     }
                 }
             }
@@ -406,6 +412,7 @@ int tile_dispatch(const PlaneArgs* a, const TileBatch* b, int field, bool hasmp,
         if (WX == 64 && WY == 64) return tile_fm<26, 64, 64>(a, b, field, hasmp, planes, s);
         if (WX == 64 && WY == 32) return tile_fm<26, 64, 32>(a, b, field, hasmp, planes, s);
         if (WX == 128 && WY == 32) return tile_fm<26, 128, 32>(a, b, field, hasmp, planes, s);
+        if (WX == 64 && WY == 40) return tile_fm<26, 64, 40>(a, b, field, hasmp, planes, s);
     }
     return set_error(HP_ERR_ARG, "sweep: no tile kernel of this shape");
 }

@@ -109,7 +109,7 @@ def test_sweep_full_size_2d_moore_two_mcs(oracle, variant):
     assert hm.hp_sweep_status() == 0
 
 
-@pytest.mark.parametrize("variant", [2, 4, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", [2, 4, 6, 7, 8, 9, 10, 11, 12])
 def test_sweep_full_size_3d_point_field_one_mcs(oracle, variant):
     """512^3 26-neighbour lattice with a per-material-point field: one MCS bit-exact."""
     torch, hm = need_gpu()
