@@ -223,13 +223,14 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
         // ---- A: interior test, queue the rest ---------------------------------
         constexpr int RSTEP = NBR == 4 ? 1 : 2;
         const int rstart = NBR == 4 ? lo : lo + ((lo ^ (p >> 1)) & 1);
-        for (int r0 = rstart; r0 < hiy; r0 += RSTEP * RPP) {
-            const int r = r0 + RSTEP * rs;
+        // one quad of row r: sites ca = c0 + px and cb = ca + 2; bits 0/1 of
+        // the result say which of them need the Metropolis stage
+        auto item = [&](const int r, int& ca, int& cb) -> uint32_t {
             const int px = NBR == 4 ? ((r + p) & 1) : (p & 1);
-            const int ca = c0 + px, cb = ca + 2;
+            const int ca_ = c0 + px, cb_ = ca_ + 2;
             const bool rowok = r < hiy;
-            const bool va = rowok && ca >= lo && ca < hi;
-            const bool vb = rowok && cb >= lo && cb < hi;
+            const bool va = rowok && ca_ >= lo && ca_ < hi;
+            const bool vb = rowok && cb_ >= lo && cb_ < hi;
             // every lane loads (lanes past the last row read row hiy - 1 and
             // discard it) so that the edge columns can come from the
             // neighbouring lanes: the left lane's last column and the right
@@ -268,14 +269,27 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
                     }
                 }
             }
-            const bool ba = va && acc0 != 0u, bb = vb && acc1 != 0u;
-            const unsigned ma = __ballot_sync(0xFFFFFFFFu, ba), mbb = __ballot_sync(0xFFFFFFFFu, bb);
-            if (ma | mbb) {
+            ca = ca_;
+            cb = cb_;
+            return (va && acc0 != 0u ? 1u : 0u) | (vb && acc1 != 0u ? 2u : 0u);
+        };
+        // two rows per trip: their loads and shuffles overlap
+        for (int r0 = rstart; r0 < hiy; r0 += 2 * RSTEP * RPP) {
+            const int r1 = r0 + RSTEP * rs, r2 = r1 + RSTEP * RPP;
+            int ca1, cb1, ca2, cb2;
+            const uint32_t f1 = item(r1, ca1, cb1);
+            const uint32_t f2 = item(r2, ca2, cb2);
+            const unsigned m0 = __ballot_sync(0xFFFFFFFFu, f1 & 1u), m1 = __ballot_sync(0xFFFFFFFFu, f1 & 2u);
+            const unsigned m2 = __ballot_sync(0xFFFFFFFFu, f2 & 1u), m3 = __ballot_sync(0xFFFFFFFFu, f2 & 2u);
+            if (m0 | m1 | m2 | m3) {
+                const int n0 = __popc(m0), n1 = __popc(m1), n2 = __popc(m2);
                 int k = 0;
-                if (lane == 0) k = atomicAdd(qn + p, __popc(ma) + __popc(mbb));
+                if (lane == 0) k = atomicAdd(qn + p, n0 + n1 + n2 + __popc(m3));
                 k = __shfl_sync(0xFFFFFFFFu, k, 0);
-                if (ba) queue[k + __popc(ma & lt)] = ((uint32_t)r << 8) | (uint32_t)ca;
-                if (bb) queue[k + __popc(ma) + __popc(mbb & lt)] = ((uint32_t)r << 8) | (uint32_t)cb;
+                if (f1 & 1u) queue[k + __popc(m0 & lt)] = ((uint32_t)r1 << 8) | (uint32_t)ca1;
+                if (f1 & 2u) queue[k + n0 + __popc(m1 & lt)] = ((uint32_t)r1 << 8) | (uint32_t)cb1;
+                if (f2 & 1u) queue[k + n0 + n1 + __popc(m2 & lt)] = ((uint32_t)r2 << 8) | (uint32_t)ca2;
+                if (f2 & 2u) queue[k + n0 + n1 + n2 + __popc(m3 & lt)] = ((uint32_t)r2 << 8) | (uint32_t)cb2;
             }
         }
         __syncthreads();
@@ -327,7 +341,7 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
 }
 
 template <int NBR, int WX, int WY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const __grid_constant__ PlaneArgs a) {
+__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 4 : 5) k_tile(const __grid_constant__ PlaneArgs a) {
     extern __shared__ __align__(16) unsigned char raw[];
     tile_body<NBR, WX, WY, FIELD, HASMP>(a, (int)blockIdx.x, (int)blockIdx.y, raw);
 }
@@ -335,7 +349,7 @@ __global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4) k_tile(const 
 // Many independent lattices in one launch: block b belongs to the replica r
 // with start[r] <= b < start[r+1]; within it b - start[r] = zidx * tiles + tile.
 template <int NBR, int WX, int WY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 3 : 4)
+__global__ void __launch_bounds__(kTileThreads, NBR == 26 ? 4 : 5)
     k_tile_batch(const PlaneArgs* __restrict__ args, const int64_t* __restrict__ start, int R, uint32_t sweep_add) {
     extern __shared__ __align__(16) unsigned char raw[];
     __shared__ PlaneArgs sa;
