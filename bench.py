@@ -170,6 +170,11 @@ class Job:
         self.measure()
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, ncu capture of the
+# 4096^2 Moore workload, keyed by (neighbours, tile variant)
+MEASURED_TRAFFIC = {(8, 10): 68.120064e6 + 20.746240e6}
+
+
 def sweep_kernel_name(nbr, variant):
     """Kernel family of a fused-sweep tile variant (variant numbering of hp_sweep_variants)."""
     v = int(variant or 0)
@@ -236,9 +241,11 @@ def run_ours(args, rank, world, local_rank):
             "kernel": sweep_kernel_name(W.nbr, job.tuned.get("variant") if job.tuned else 0),
             "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
             "sweep_site_updates_per_s": round(job.N / per_launch_s, 1)}
-    traffic = os.environ.get("HP_SWEEP_TRAFFIC_BYTES")
-    if traffic:
-        roof["traffic"] = float(traffic)
+    # DRAM bytes of one launch of the kernel, from an ncu capture of that exact
+    # variant (profiles/k_tile8_2d4096_moore.md); null for any other kernel
+    traffic = MEASURED_TRAFFIC.get((W.nbr, job.tuned.get("variant") if job.tuned else None))
+    if traffic is not None:
+        roof["traffic"] = traffic
 
     e2e = None
     if not args.no_e2e:
