@@ -94,8 +94,8 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
     return {"wall_s": wall, "field_s": t_field, **tex}
 
 
-def train_surrogate(torch, prm, n_orient=16384, K=32, n_incr=20, steps=20000, lr=3e-3, seed=3000, log_every=0,
-                    batch=32768):
+def train_surrogate(torch, prm, n_orient=65536, K=128, n_incr=20, steps=60000, lr=2e-3, seed=3000, log_every=0,
+                    batch=65536):
     """Generate samples with the MCP kernel and fit the network with the tensor-core kernels,
     Adam on contiguous minibatches of `batch` rows taken in turn (rows are orientation-major,
     so each minibatch holds whole orientations at every increment; batch=None uses all rows).

@@ -73,18 +73,19 @@ def trained():
     torch, hm = need_gpu()
     from paper_1007_3509_gb300 import hybrid
     prm = hybrid.cp_params_table1(1e-4, 7.0)
-    params, load, L, hist = hybrid.train_surrogate(torch, prm, log_every=1000)
+    params, load, L, hist = hybrid.train_surrogate(torch, prm, log_every=5000)
     return params, load, L, hist, prm
 
 
 def test_surrogate_accuracy_against_many_histories(trained):
-    """Held-out orientations, targets averaged over 512 histories (their own noise
-    is about 0.75 %): the network's driving field w + E_rho is within 2.5e-2
-    relative (L2 over samples); about 1.7 % is measured."""
+    """Held-out orientations, targets averaged over 4096 histories (their own
+    noise is about 0.27 %): the network's driving field w + E_rho is within 1e-2
+    relative (L2 over samples) of the plain solver's expectation; about 0.9 % is
+    measured."""
     torch, hm = need_gpu()
     params, load, L, hist, prm = trained
     assert hist[-1][1] < hist[0][1]
-    n_orient, K, n_incr = 256, 512, 20
+    n_orient, K, n_incr = 256, 4096, 20
     quat = torch.empty(n_orient, 4, device="cuda")
     hm.hp_orientations(n_orient, 999, hm.ORIENT_SO3, quat)
     X = torch.empty(n_orient * n_incr, 11, device="cuda")
@@ -98,7 +99,7 @@ def test_surrogate_accuracy_against_many_histories(trained):
     e_sur = p[:, 0] * SC[2] + p[:, 1] * SC[3]
     err = np.linalg.norm(e_sur - e_ref) / np.linalg.norm(e_ref)
     print(f"surrogate relative field error {err:.4f}; final training loss {L:.3e}")
-    assert err <= 2.5e-2
+    assert err <= 1e-2
 
 
 def test_surrogate_hybrid_matches_plain_texture(trained):
