@@ -295,12 +295,14 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
         __syncthreads();
         // ---- B: Metropolis update of the queued sites, two per thread --------
         const uint32_t colour = NBR == 4 ? (uint32_t)p : cz + (uint32_t)p;
-        // B1: each thread draws for two queued sites; the proposals of another
-        // grain go to its warp's queue.  B2: the warp tests them, all lanes busy.
+        // B1: each warp takes the next 64 queued sites (two per lane), so that
+        // when the queue is short a few warps are busy and the rest skip; the
+        // proposals of another grain go to the warp's queue.  B2: the warp
+        // tests them, all lanes busy.
         const int n = qn[p];
         uint2* wq = wqueue + 64 * (threadIdx.x >> 5);
         for (int k0 = 0; k0 < n; k0 += 2 * kTileThreads) {
-            const int k1 = k0 + (int)threadIdx.x, k2 = k1 + kTileThreads;
+            const int k1 = k0 + 64 * (int)(threadIdx.x >> 5) + lane, k2 = k1 + 32;
             uint2 w1 = make_uint2(0u, 0u), w2 = make_uint2(0u, 0u);
             const bool a1 = k1 < n && t.draw_site(queue[k1], colour, w1);
             const bool a2 = k2 < n && t.draw_site(queue[k2], colour, w2);
