@@ -124,3 +124,35 @@ def test_sweep_full_size_3d_point_field_one_mcs(oracle, variant):
                           variant=variant)
     np.testing.assert_array_equal(q, ref_q)
     np.testing.assert_array_equal(mp, ref_mp)
+
+
+@pytest.mark.parametrize("kind", ["monotone", "perturbed"])
+@pytest.mark.parametrize("variant", [0, 10])
+def test_sweep_arbitrary_threshold_table(oracle, kind, variant):
+    """The threshold table is input data: a table that is not of the exp form (any
+    monotone table, or an exp table with one entry moved) gives the oracle's
+    lattice too, on the plane and the tile kernels."""
+    torch, hm = need_gpu()
+    L, nbr, Q = (200, 130), 8, 9
+    q0, bgrain, _, _ = _inputs(L, Q, 41)
+    thr, D = oracle.threshold_table(0.8)
+    thr = thr.copy()
+    if kind == "monotone":
+        rng = np.random.default_rng(5)
+        thr[1:] = np.sort(rng.integers(1, 2**32 - 2, size=D, dtype=np.uint64))[::-1].astype(np.uint32)
+    else:
+        thr[256] = np.uint32(int(thr[256]) // 2)   # d = 256: one unlike bond and no field change
+    seed, n = 1234, 3
+    ref_q, _, _, _ = oracle.sweep(2, L, nbr, 256, seed, 0, n, thr, D, q0, bgrain[q0], None)
+    lat = hm.Lattice(2, L, nbr, 256, seed, Q, hm.FIELD_GRAIN)
+    q = torch.from_numpy(q0.copy()).cuda()
+    lat.hp_bind(q, None)
+    tab = torch.from_numpy(bgrain).cuda()
+    lat.hp_set_field(tab)
+    lat.hp_set_threshold_table(thr, D)
+    lat.hp_set_sweep_kernel(0)
+    lat.hp_set_sweep_variant(variant)
+    lat.hp_sweep(n)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(q.cpu().numpy(), ref_q)
+    lat.close()
