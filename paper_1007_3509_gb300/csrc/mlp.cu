@@ -14,8 +14,9 @@
 // Tensor-core layout: operands in shared memory use the canonical K-major
 // layout without swizzle -- 8x8 BF16 core matrices of 128 contiguous bytes,
 // consecutive along K (leading byte offset 128), row groups of 8 rows
-// 16*K bytes apart (stride byte offset).  One CTA = 4 warps = one 128-row tile
-// at a time (row r = thread r = TMEM lane r).  A single thread issues the
+// 16*K bytes apart (stride byte offset).  One CTA = one 128-row tile at a time:
+// inference with 4 warps (row r = thread r = TMEM lane r), training with 8
+// warps (two threads per row, 32 features each).  A single thread issues the
 // MMAs and commits them to an mbarrier; all waits are bounded by a clock
 // budget after which the kernel raises an error flag and leaves cleanly.
 #include <cuda_bf16.h>
@@ -159,30 +160,6 @@ __device__ void stage_weight(unsigned char* dst, const float* W, int N, int Krea
     }
 }
 
-// stage W^T: element (n, k) = W[k][n] for W [Kdim][N] (both 64 here)
-__device__ void stage_weight_t(unsigned char* dst, const float* W, int N, int K) {
-    for (int idx = threadIdx.x; idx < N * K; idx += NT) {
-        const int n = idx / K, k = idx - n * K;
-        *reinterpret_cast<__nv_bfloat16*>(dst + canon(n, k, K)) = __float2bfloat16_rn(W[k * N + n]);
-    }
-}
-
-// Sum 64 per-lane values over the 32 lanes of a warp; lane l ends with the sums
-// of features 2l and 2l+1 in v[0], v[1] (a butterfly reduce-scatter).
-__device__ __forceinline__ void warp_reduce_scatter64(float* v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int m = 16, half = 32; m >= 1; m >>= 1, half >>= 1) {
-        const bool up = lane & m;
-#pragma unroll
-        for (int i = 0; i < half; ++i) {
-            const float a = v[i], b = v[i + half];
-            const float send = up ? a : b, keep = up ? b : a;
-            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, m);
-        }
-    }
-}
-
 __device__ __forceinline__ void sync_for_mma() {
     fence_async_smem();
     fence_before();
@@ -319,6 +296,7 @@ struct TrainSmem {
     alignas(1024) unsigned char dzt[TILE * TILE * 2];// A of dW (M = 128: 64 features + 64 zero rows, K = rows)
     float b1[HID], b2[HID], b3[HID], w4[OUT * HID], b4[OUT];
     float gb1[HID], gb2[HID], gb3[HID], gw4[OUT * HID], gb4[OUT], loss;
+    float2 yp[2][TILE];  // the two halves' shares of the output layer, per row
     alignas(8) unsigned long long mbar;
     uint32_t tmem;
 };
@@ -326,30 +304,80 @@ struct TrainSmem {
 // TMEM columns
 constexpr uint32_t CZ1 = 0, CZ2 = 64, CZ3 = 128, CDH = 192, CDW3 = 256, CDW2 = 320, CDW1 = 384;
 
-__global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P, const float* __restrict__ X,
-                                                     const float* __restrict__ T, int64_t M, float inv_batch,
-                                                     float* __restrict__ grads, float* __restrict__ loss, int* err) {
+// Training runs two threads per row: warp w serves TMEM lane quadrant w % 4
+// (rows 32 (w % 4) .. + 31) and features 32 (w / 4) .. + 31 of every layer,
+// so that each thread's element-wise work, and its unrolled code, is half a row.
+constexpr int NTT = 2 * TILE;
+
+// chunks c0 .. c0 + NCH - 1 (8 values each, v[0 .. 8 NCH)) of row r of a K-major operand
+template <int K, int NCH>
+__device__ __forceinline__ void put_row_part(unsigned char* base, int r, int c0, const float* v) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        __align__(16) __nv_bfloat16 t[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = __float2bfloat16_rn(v[8 * c + j]);
+        *reinterpret_cast<int4*>(base + canon(r, 8 * (c0 + c), K)) = *reinterpret_cast<const int4*>(t);
+    }
+}
+
+// v[i] at (f0 + i, col) for i < N of a ROWS x K operand
+template <int N, int K>
+__device__ __forceinline__ void put_col_off(unsigned char* base, int col, int f0, const float* v) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        *reinterpret_cast<__nv_bfloat16*>(base + canon(f0 + i, col, K)) = __float2bfloat16_rn(v[i]);
+}
+
+// Sum 32 per-lane values over the 32 lanes of a warp; lane l ends with the sum
+// of value l in v[0] (a butterfly reduce-scatter).
+__device__ __forceinline__ void warp_reduce_scatter32(float* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 16, half = 16; m >= 1; m >>= 1, half >>= 1) {
+        const bool up = lane & m;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float a = v[i], b = v[i + half];
+            const float send = up ? a : b, keep = up ? b : a;
+            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, m);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ P, const float* __restrict__ X,
+                                                      const float* __restrict__ T, int64_t M, float inv_batch,
+                                                      float* __restrict__ grads, float* __restrict__ loss, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, hf = warp >> 2;
+    const int r = quad * 32 + lane;  // row of the tile = TMEM lane
+    const int f0 = 32 * hf;          // first feature of this thread
     if (warp == 0) tmem_alloc(saddr(&S.tmem), 512);
     if (tid == 0) {
         mbar_init(saddr(&S.mbar));
         S.loss = 0.0f;
     }
-    stage_weight(S.w1, P + OW1, HID, IN, INP);
-    stage_weight(S.w2, P + OW2, HID, HID, HID);
-    stage_weight(S.w3, P + OW3, HID, HID, HID);
-    stage_weight_t(S.w2t, P + OW2, HID, HID);
-    stage_weight_t(S.w3t, P + OW3, HID, HID);
-    for (int i = tid; i < TILE * TILE * 2 / 16; i += NT) reinterpret_cast<int4*>(S.dzt)[i] = make_int4(0, 0, 0, 0);
-    for (int i = tid; i < HID; i += NT) {
+    for (int idx = tid; idx < HID * INP; idx += NTT) {
+        const int n = idx / INP, k = idx - n * INP;
+        *reinterpret_cast<__nv_bfloat16*>(S.w1 + canon(n, k, INP)) = __float2bfloat16_rn(k < IN ? P[OW1 + n * IN + k] : 0.0f);
+    }
+    for (int idx = tid; idx < HID * HID; idx += NTT) {
+        const int n = idx / HID, k = idx - n * HID;
+        *reinterpret_cast<__nv_bfloat16*>(S.w2 + canon(n, k, HID)) = __float2bfloat16_rn(P[OW2 + n * HID + k]);
+        *reinterpret_cast<__nv_bfloat16*>(S.w3 + canon(n, k, HID)) = __float2bfloat16_rn(P[OW3 + n * HID + k]);
+        *reinterpret_cast<__nv_bfloat16*>(S.w2t + canon(n, k, HID)) = __float2bfloat16_rn(P[OW2 + k * HID + n]);
+        *reinterpret_cast<__nv_bfloat16*>(S.w3t + canon(n, k, HID)) = __float2bfloat16_rn(P[OW3 + k * HID + n]);
+    }
+    for (int i = tid; i < TILE * TILE * 2 / 16; i += NTT) reinterpret_cast<int4*>(S.dzt)[i] = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < HID; i += NTT) {
         S.b1[i] = P[OB1 + i];
         S.b2[i] = P[OB2 + i];
         S.b3[i] = P[OB3 + i];
         S.gb1[i] = S.gb2[i] = S.gb3[i] = 0.0f;
     }
-    for (int i = tid; i < OUT * HID; i += NT) {
+    for (int i = tid; i < OUT * HID; i += NTT) {
         S.w4[i] = bf16r(P[OW4 + i]);
         S.gw4[i] = 0.0f;
     }
@@ -360,12 +388,12 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
     sync_for_mma();
     const uint32_t tm = S.tmem;
     const uint32_t mbar = saddr(&S.mbar);
-    const uint32_t lb = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lb = tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)f0;
     uint32_t phase = 0;
     const int64_t ntiles = (M + TILE - 1) / TILE;
     bool ok = true;
     uint32_t first = 1;  // first tile of this CTA: weight-gradient accumulators start from zero
-    float v[HID], z[HID];
+    float v[32], z[32];
     float my_loss = 0.0f, gb4_0 = 0.0f, gb4_1 = 0.0f;
 
     auto wait_mma = [&]() -> bool {
@@ -375,16 +403,24 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
         fence_after();
         return !any_bad;
     };
+    // bias gradient of this thread's 32 features summed over the warp's 32 rows
+    auto bias_grad = [&](float* g) {
+        warp_reduce_scatter32(v);
+        atomicAdd(&g[f0 + lane], v[0]);
+    };
 
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int64_t row = t * TILE + tid;
+        const int64_t row = t * TILE + r;
         const bool valid = row < M;
-        {
-            float xr[INP];
+        {   // inputs 8 hf .. 8 hf + 7 of this row
+            float xr[8];
 #pragma unroll
-            for (int k = 0; k < INP; ++k) xr[k] = (k < IN && valid) ? X[row * IN + k] : 0.0f;
-            put_row<INP>(S.x, tid, xr);
-            put_col<INP, TILE>(S.xt, tid, xr);
+            for (int k = 0; k < 8; ++k) {
+                const int f = 8 * hf + k;
+                xr[k] = (f < IN && valid) ? X[row * IN + f] : 0.0f;
+            }
+            put_row_part<INP, 1>(S.x, r, hf, xr);
+            put_col_off<8, TILE>(S.xt, r, 8 * hf, xr);
         }
         sync_for_mma();
         // ---- forward ------------------------------------------------------
@@ -393,11 +429,11 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld64(lb + CZ1, v);
+        tmem_ld32(lb + CZ1, v);
 #pragma unroll
-        for (int k = 0; k < HID; ++k) v[k] = gelu(v[k] + S.b1[k]);
-        put_row<HID>(S.h1, tid, v);
-        put_col<HID, TILE>(S.h1t, tid, v);
+        for (int k = 0; k < 32; ++k) v[k] = gelu(v[k] + S.b1[f0 + k]);
+        put_row_part<HID, 4>(S.h1, r, 4 * hf, v);
+        put_col_off<32, TILE>(S.h1t, r, f0, v);
         sync_for_mma();
         if (tid == 0) {
 #pragma unroll
@@ -407,11 +443,11 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld64(lb + CZ2, v);
+        tmem_ld32(lb + CZ2, v);
 #pragma unroll
-        for (int k = 0; k < HID; ++k) v[k] = gelu(v[k] + S.b2[k]);
-        put_row<HID>(S.h2, tid, v);
-        put_col<HID, TILE>(S.h2t, tid, v);
+        for (int k = 0; k < 32; ++k) v[k] = gelu(v[k] + S.b2[f0 + k]);
+        put_row_part<HID, 4>(S.h2, r, 4 * hf, v);
+        put_col_off<32, TILE>(S.h2t, r, f0, v);
         sync_for_mma();
         if (tid == 0) {
 #pragma unroll
@@ -421,45 +457,48 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld64(lb + CZ3, z);
+        tmem_ld32(lb + CZ3, z);
         // ---- output layer, loss, dz3 ---------------------------------------
-        float y0 = S.b4[0], y1 = S.b4[1];
+        float p0 = 0.0f, p1 = 0.0f;  // this half's share of y
 #pragma unroll
-        for (int k = 0; k < HID; ++k) {
-            z[k] += S.b3[k];
+        for (int k = 0; k < 32; ++k) {
+            z[k] += S.b3[f0 + k];
             v[k] = bf16r(gelu(z[k]));  // h3
-            y0 = fmaf(v[k], S.w4[k], y0);
-            y1 = fmaf(v[k], S.w4[HID + k], y1);
+            p0 = fmaf(v[k], S.w4[f0 + k], p0);
+            p1 = fmaf(v[k], S.w4[HID + f0 + k], p1);
         }
+        S.yp[hf][r] = make_float2(p0, p1);
+        __syncthreads();
+        const float2 ya = S.yp[0][r], yb = S.yp[1][r];
+        const float y0 = S.b4[0] + ya.x + yb.x, y1 = S.b4[1] + ya.y + yb.y;
         float d0 = 0.0f, d1 = 0.0f;
         if (valid) {
             const float e0 = y0 - T[row * OUT + 0], e1 = y1 - T[row * OUT + 1];
-            my_loss += e0 * e0 + e1 * e1;
+            if (hf == 0) my_loss += e0 * e0 + e1 * e1;
             d0 = e0 * inv_batch;
             d1 = e1 * inv_batch;
         }
-        gb4_0 += d0;
-        gb4_1 += d1;
+        if (hf == 0) {
+            gb4_0 += d0;
+            gb4_1 += d1;
+        }
         {   // dW4[o][k] = sum_rows d_o h3_k
-            float g[HID];
+            float g[32];
 #pragma unroll
-            for (int k = 0; k < HID; ++k) g[k] = d0 * v[k];
-            warp_reduce_scatter64(g);
-            atomicAdd(&S.gw4[2 * lane], g[0]);
-            atomicAdd(&S.gw4[2 * lane + 1], g[1]);
+            for (int k = 0; k < 32; ++k) g[k] = d0 * v[k];
+            warp_reduce_scatter32(g);
+            atomicAdd(&S.gw4[f0 + lane], g[0]);
 #pragma unroll
-            for (int k = 0; k < HID; ++k) g[k] = d1 * v[k];
-            warp_reduce_scatter64(g);
-            atomicAdd(&S.gw4[HID + 2 * lane], g[0]);
-            atomicAdd(&S.gw4[HID + 2 * lane + 1], g[1]);
+            for (int k = 0; k < 32; ++k) g[k] = d1 * v[k];
+            warp_reduce_scatter32(g);
+            atomicAdd(&S.gw4[HID + f0 + lane], g[0]);
         }
 #pragma unroll
-        for (int k = 0; k < HID; ++k) v[k] = (d0 * S.w4[k] + d1 * S.w4[HID + k]) * gelu_grad(z[k]);  // dz3
-        put_row<HID>(S.dz, tid, v);
-        put_col<HID, TILE>(S.dzt, tid, v);
-        warp_reduce_scatter64(v);
-        atomicAdd(&S.gb3[2 * lane], v[0]);
-        atomicAdd(&S.gb3[2 * lane + 1], v[1]);
+        for (int k = 0; k < 32; ++k)
+            v[k] = (d0 * S.w4[f0 + k] + d1 * S.w4[HID + f0 + k]) * gelu_grad(z[k]);  // dz3
+        put_row_part<HID, 4>(S.dz, r, 4 * hf, v);
+        put_col_off<32, TILE>(S.dzt, r, f0, v);
+        bias_grad(S.gb3);
         sync_for_mma();
         // ---- dh2 = dz3 W3, dW3 += dz3^T h2 ---------------------------------
         if (tid == 0) {
@@ -474,15 +513,13 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld64(lb + CDH, v);
-        tmem_ld64(lb + CZ2, z);
+        tmem_ld32(lb + CDH, v);
+        tmem_ld32(lb + CZ2, z);
 #pragma unroll
-        for (int k = 0; k < HID; ++k) v[k] *= gelu_grad(z[k] + S.b2[k]);  // dz2
-        put_row<HID>(S.dz, tid, v);
-        put_col<HID, TILE>(S.dzt, tid, v);
-        warp_reduce_scatter64(v);
-        atomicAdd(&S.gb2[2 * lane], v[0]);
-        atomicAdd(&S.gb2[2 * lane + 1], v[1]);
+        for (int k = 0; k < 32; ++k) v[k] *= gelu_grad(z[k] + S.b2[f0 + k]);  // dz2
+        put_row_part<HID, 4>(S.dz, r, 4 * hf, v);
+        put_col_off<32, TILE>(S.dzt, r, f0, v);
+        bias_grad(S.gb2);
         sync_for_mma();
         // ---- dh1 = dz2 W2, dW2 += dz2^T h1 ---------------------------------
         if (tid == 0) {
@@ -497,14 +534,12 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld64(lb + CDH, v);
-        tmem_ld64(lb + CZ1, z);
+        tmem_ld32(lb + CDH, v);
+        tmem_ld32(lb + CZ1, z);
 #pragma unroll
-        for (int k = 0; k < HID; ++k) v[k] *= gelu_grad(z[k] + S.b1[k]);  // dz1
-        put_col<HID, TILE>(S.dzt, tid, v);
-        warp_reduce_scatter64(v);
-        atomicAdd(&S.gb1[2 * lane], v[0]);
-        atomicAdd(&S.gb1[2 * lane + 1], v[1]);
+        for (int k = 0; k < 32; ++k) v[k] *= gelu_grad(z[k] + S.b1[f0 + k]);  // dz1
+        put_col_off<32, TILE>(S.dzt, r, f0, v);
+        bias_grad(S.gb1);
         sync_for_mma();
         // ---- dW1 += dz1^T x -------------------------------------------------
         if (tid == 0) {
@@ -519,25 +554,23 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
     }
     // ---- flush this CTA's gradients ------------------------------------------
     if (ok && !first) {
-        // weight gradients: TMEM lanes 0..63 (warps 0 and 1) hold dW rows (out features)
-        if (warp < 2) {
-            const int o = tid;  // out feature
-            tmem_ld64(lb + CDW3, v);
+        // weight gradients: TMEM lanes 0..63 (quadrants 0 and 1) hold dW rows
+        // (out features); each half of the warps takes 32 of the columns
+        if (quad < 2) {
+            const int o = r;  // out feature
+            tmem_ld32(lb + CDW3, v);
 #pragma unroll
-            for (int k = 0; k < HID; ++k) atomicAdd(&grads[OW3 + o * HID + k], v[k]);
-            tmem_ld64(lb + CDW2, v);
+            for (int k = 0; k < 32; ++k) atomicAdd(&grads[OW3 + o * HID + f0 + k], v[k]);
+            tmem_ld32(lb + CDW2, v);
 #pragma unroll
-            for (int k = 0; k < HID; ++k) atomicAdd(&grads[OW2 + o * HID + k], v[k]);
-            tmem_ld32(lb + CDW1, v);  // 32 columns: the first 16 hold dW1
+            for (int k = 0; k < 32; ++k) atomicAdd(&grads[OW2 + o * HID + f0 + k], v[k]);
+            if (hf == 0) {
+                tmem_ld32(lb + CDW1, v);  // the first 16 columns hold dW1
 #pragma unroll
-            for (int k = 0; k < IN; ++k) atomicAdd(&grads[OW1 + o * IN + k], v[k]);
-        } else {
-            // keep every warp in the aligned tcgen05.ld pattern
-            tmem_ld64(lb + CDW3, v);
-            tmem_ld64(lb + CDW2, v);
-            tmem_ld32(lb + CDW1, v);
+                for (int k = 0; k < IN; ++k) atomicAdd(&grads[OW1 + o * IN + k], v[k]);
+            }
         }
-        // per-row reductions of the loss and b4 gradient
+        // per-row reductions of the loss and b4 gradient (the second half adds zeros)
         for (int m = 16; m >= 1; m >>= 1) {
             my_loss += __shfl_xor_sync(0xFFFFFFFFu, my_loss, m);
             gb4_0 += __shfl_xor_sync(0xFFFFFFFFu, gb4_0, m);
@@ -549,12 +582,12 @@ __global__ void __launch_bounds__(NT, 1) k_mlp_train(const float* __restrict__ P
             atomicAdd(&S.gb4[1], gb4_1);
         }
         __syncthreads();
-        for (int i = tid; i < HID; i += NT) {
+        for (int i = tid; i < HID; i += NTT) {
             atomicAdd(&grads[OB1 + i], S.gb1[i]);
             atomicAdd(&grads[OB2 + i], S.gb2[i]);
             atomicAdd(&grads[OB3 + i], S.gb3[i]);
         }
-        for (int i = tid; i < OUT * HID; i += NT) atomicAdd(&grads[OW4 + i], S.gw4[i]);
+        for (int i = tid; i < OUT * HID; i += NTT) atomicAdd(&grads[OW4 + i], S.gw4[i]);
         if (tid < OUT) atomicAdd(&grads[OB4 + tid], S.gb4[tid]);
         if (tid == 0 && loss) atomicAdd(loss, S.loss * 0.5f * inv_batch);
     }
@@ -650,7 +683,7 @@ extern "C" int hp_mlp_gradients(const float* params, const float* X, const float
     const int64_t tiles = (M + TILE - 1) / TILE;
     const int64_t grid = tiles < sm_count() ? tiles : sm_count();
     ::hp::count_launch();
-    k_mlp_train<<<(unsigned)grid, NT, smem, s>>>(params, X, T, M, 1.0f / (float)M, grads, loss, err);
+    k_mlp_train<<<(unsigned)grid, NTT, smem, s>>>(params, X, T, M, 1.0f / (float)M, grads, loss, err);
     HP_LAUNCH_CHECK("k_mlp_train");
     return HP_OK;
 }
