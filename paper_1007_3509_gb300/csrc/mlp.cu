@@ -15,8 +15,8 @@
 // layout without swizzle -- 8x8 BF16 core matrices of 128 contiguous bytes,
 // consecutive along K (leading byte offset 128), row groups of 8 rows
 // 16*K bytes apart (stride byte offset).  One CTA = one 128-row tile at a time:
-// inference with 4 warps (row r = thread r = TMEM lane r), training with 8
-// warps (two threads per row, 32 features each).  A single thread issues the
+// inference with 4 warps (row r = thread r = TMEM lane r), training with 16
+// warps (four threads per row, 16 features each).  A single thread issues the
 // MMAs and commits them to an mbarrier; all waits are bounded by a clock
 // budget after which the kernel raises an error flag and leaves cleanly.
 #include <cuda_bf16.h>
@@ -296,7 +296,7 @@ struct TrainSmem {
     alignas(1024) unsigned char dzt[TILE * TILE * 2];// A of dW (M = 128: 64 features + 64 zero rows, K = rows)
     float b1[HID], b2[HID], b3[HID], w4[OUT * HID], b4[OUT];
     float gb1[HID], gb2[HID], gb3[HID], gw4[OUT * HID], gb4[OUT], loss;
-    float2 yp[2][TILE];  // the two halves' shares of the output layer, per row
+    float2 yp[4][TILE];  // each feature group's share of the output layer, per row
     alignas(8) unsigned long long mbar;
     uint32_t tmem;
 };
@@ -304,10 +304,11 @@ struct TrainSmem {
 // TMEM columns
 constexpr uint32_t CZ1 = 0, CZ2 = 64, CZ3 = 128, CDH = 192, CDW3 = 256, CDW2 = 320, CDW1 = 384;
 
-// Training runs two threads per row: warp w serves TMEM lane quadrant w % 4
-// (rows 32 (w % 4) .. + 31) and features 32 (w / 4) .. + 31 of every layer,
-// so that each thread's element-wise work, and its unrolled code, is half a row.
-constexpr int NTT = 2 * TILE;
+// Training runs NH threads per row: warp w serves TMEM lane quadrant w % 4
+// (rows 32 (w % 4) .. + 31) and features FW (w / 4) .. + FW - 1 of every
+// layer, so that each thread's element-wise work, and its unrolled code, is
+// 1/NH of a row.
+constexpr int NH = 4, FW = HID / NH, NTT = NH * TILE;
 
 // chunks c0 .. c0 + NCH - 1 (8 values each, v[0 .. 8 NCH)) of row r of a K-major operand
 template <int K, int NCH>
@@ -329,12 +330,14 @@ __device__ __forceinline__ void put_col_off(unsigned char* base, int col, int f0
         *reinterpret_cast<__nv_bfloat16*>(base + canon(f0 + i, col, K)) = __float2bfloat16_rn(v[i]);
 }
 
-// Sum 32 per-lane values over the 32 lanes of a warp; lane l ends with the sum
-// of value l in v[0] (a butterfly reduce-scatter).
-__device__ __forceinline__ void warp_reduce_scatter32(float* v) {
+// Sum N (16 or 32) per-lane values over the 32 lanes of a warp (a butterfly
+// reduce-scatter): lane l ends with the sum of value l / (32 / N) in v[0].
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter(float* v) {
     const int lane = threadIdx.x & 31;
+    int m = 16;
 #pragma unroll
-    for (int m = 16, half = 16; m >= 1; m >>= 1, half >>= 1) {
+    for (int half = N / 2; half >= 1; half >>= 1, m >>= 1) {
         const bool up = lane & m;
 #pragma unroll
         for (int i = 0; i < half; ++i) {
@@ -342,6 +345,25 @@ __device__ __forceinline__ void warp_reduce_scatter32(float* v) {
             const float send = up ? a : b, keep = up ? b : a;
             v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, m);
         }
+    }
+#pragma unroll
+    for (; m >= 1; m >>= 1) v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], m);
+}
+
+// FW consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ldw(uint32_t taddr, float* v) {
+    if (FW == 32) {
+        tmem_ld32(taddr, v);
+    } else {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
     }
 }
 
@@ -353,7 +375,8 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, hf = warp >> 2;
     const int r = quad * 32 + lane;  // row of the tile = TMEM lane
-    const int f0 = 32 * hf;          // first feature of this thread
+    const int f0 = FW * hf;          // first feature of this thread
+    constexpr int RL = 32 / FW;      // lanes holding each feature after a reduce-scatter
     if (warp == 0) tmem_alloc(saddr(&S.tmem), 512);
     if (tid == 0) {
         mbar_init(saddr(&S.mbar));
@@ -393,7 +416,7 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
     const int64_t ntiles = (M + TILE - 1) / TILE;
     bool ok = true;
     uint32_t first = 1;  // first tile of this CTA: weight-gradient accumulators start from zero
-    float v[32], z[32];
+    float v[FW], z[FW];
     float my_loss = 0.0f, gb4_0 = 0.0f, gb4_1 = 0.0f;
 
     auto wait_mma = [&]() -> bool {
@@ -403,16 +426,16 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         fence_after();
         return !any_bad;
     };
-    // bias gradient of this thread's 32 features summed over the warp's 32 rows
+    // bias gradient of this thread's FW features summed over the warp's 32 rows
     auto bias_grad = [&](float* g) {
-        warp_reduce_scatter32(v);
-        atomicAdd(&g[f0 + lane], v[0]);
+        warp_reduce_scatter<FW>(v);
+        if (lane % RL == 0) atomicAdd(&g[f0 + lane / RL], v[0]);
     };
 
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const int64_t row = t * TILE + r;
         const bool valid = row < M;
-        {   // inputs 8 hf .. 8 hf + 7 of this row
+        if (hf < 2) {   // inputs 8 hf .. 8 hf + 7 of this row
             float xr[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -429,11 +452,11 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld32(lb + CZ1, v);
+        tmem_ldw(lb + CZ1, v);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = gelu(v[k] + S.b1[f0 + k]);
-        put_row_part<HID, 4>(S.h1, r, 4 * hf, v);
-        put_col_off<32, TILE>(S.h1t, r, f0, v);
+        for (int k = 0; k < FW; ++k) v[k] = gelu(v[k] + S.b1[f0 + k]);
+        put_row_part<HID, FW / 8>(S.h1, r, (FW / 8) * hf, v);
+        put_col_off<FW, TILE>(S.h1t, r, f0, v);
         sync_for_mma();
         if (tid == 0) {
 #pragma unroll
@@ -443,11 +466,11 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld32(lb + CZ2, v);
+        tmem_ldw(lb + CZ2, v);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = gelu(v[k] + S.b2[f0 + k]);
-        put_row_part<HID, 4>(S.h2, r, 4 * hf, v);
-        put_col_off<32, TILE>(S.h2t, r, f0, v);
+        for (int k = 0; k < FW; ++k) v[k] = gelu(v[k] + S.b2[f0 + k]);
+        put_row_part<HID, FW / 8>(S.h2, r, (FW / 8) * hf, v);
+        put_col_off<FW, TILE>(S.h2t, r, f0, v);
         sync_for_mma();
         if (tid == 0) {
 #pragma unroll
@@ -457,11 +480,11 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld32(lb + CZ3, z);
+        tmem_ldw(lb + CZ3, z);
         // ---- output layer, loss, dz3 ---------------------------------------
         float p0 = 0.0f, p1 = 0.0f;  // this half's share of y
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < FW; ++k) {
             z[k] += S.b3[f0 + k];
             v[k] = bf16r(gelu(z[k]));  // h3
             p0 = fmaf(v[k], S.w4[f0 + k], p0);
@@ -469,8 +492,13 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         }
         S.yp[hf][r] = make_float2(p0, p1);
         __syncthreads();
-        const float2 ya = S.yp[0][r], yb = S.yp[1][r];
-        const float y0 = S.b4[0] + ya.x + yb.x, y1 = S.b4[1] + ya.y + yb.y;
+        float y0 = S.b4[0], y1 = S.b4[1];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const float2 yh = S.yp[h][r];
+            y0 += yh.x;
+            y1 += yh.y;
+        }
         float d0 = 0.0f, d1 = 0.0f;
         if (valid) {
             const float e0 = y0 - T[row * OUT + 0], e1 = y1 - T[row * OUT + 1];
@@ -483,21 +511,21 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
             gb4_1 += d1;
         }
         {   // dW4[o][k] = sum_rows d_o h3_k
-            float g[32];
+            float g[FW];
 #pragma unroll
-            for (int k = 0; k < 32; ++k) g[k] = d0 * v[k];
-            warp_reduce_scatter32(g);
-            atomicAdd(&S.gw4[f0 + lane], g[0]);
+            for (int k = 0; k < FW; ++k) g[k] = d0 * v[k];
+            warp_reduce_scatter<FW>(g);
+            if (lane % RL == 0) atomicAdd(&S.gw4[f0 + lane / RL], g[0]);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) g[k] = d1 * v[k];
-            warp_reduce_scatter32(g);
-            atomicAdd(&S.gw4[HID + f0 + lane], g[0]);
+            for (int k = 0; k < FW; ++k) g[k] = d1 * v[k];
+            warp_reduce_scatter<FW>(g);
+            if (lane % RL == 0) atomicAdd(&S.gw4[HID + f0 + lane / RL], g[0]);
         }
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
+        for (int k = 0; k < FW; ++k)
             v[k] = (d0 * S.w4[f0 + k] + d1 * S.w4[HID + f0 + k]) * gelu_grad(z[k]);  // dz3
-        put_row_part<HID, 4>(S.dz, r, 4 * hf, v);
-        put_col_off<32, TILE>(S.dzt, r, f0, v);
+        put_row_part<HID, FW / 8>(S.dz, r, (FW / 8) * hf, v);
+        put_col_off<FW, TILE>(S.dzt, r, f0, v);
         bias_grad(S.gb3);
         sync_for_mma();
         // ---- dh2 = dz3 W3, dW3 += dz3^T h2 ---------------------------------
@@ -513,12 +541,12 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld32(lb + CDH, v);
-        tmem_ld32(lb + CZ2, z);
+        tmem_ldw(lb + CDH, v);
+        tmem_ldw(lb + CZ2, z);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] *= gelu_grad(z[k] + S.b2[f0 + k]);  // dz2
-        put_row_part<HID, 4>(S.dz, r, 4 * hf, v);
-        put_col_off<32, TILE>(S.dzt, r, f0, v);
+        for (int k = 0; k < FW; ++k) v[k] *= gelu_grad(z[k] + S.b2[f0 + k]);  // dz2
+        put_row_part<HID, FW / 8>(S.dz, r, (FW / 8) * hf, v);
+        put_col_off<FW, TILE>(S.dzt, r, f0, v);
         bias_grad(S.gb2);
         sync_for_mma();
         // ---- dh1 = dz2 W2, dW2 += dz2^T h1 ---------------------------------
@@ -534,11 +562,11 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
             mma_commit(mbar);
         }
         if (!(ok = wait_mma())) break;
-        tmem_ld32(lb + CDH, v);
-        tmem_ld32(lb + CZ1, z);
+        tmem_ldw(lb + CDH, v);
+        tmem_ldw(lb + CZ1, z);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] *= gelu_grad(z[k] + S.b1[f0 + k]);  // dz1
-        put_col_off<32, TILE>(S.dzt, r, f0, v);
+        for (int k = 0; k < FW; ++k) v[k] *= gelu_grad(z[k] + S.b1[f0 + k]);  // dz1
+        put_col_off<FW, TILE>(S.dzt, r, f0, v);
         bias_grad(S.gb1);
         sync_for_mma();
         // ---- dW1 += dz1^T x -------------------------------------------------
@@ -558,14 +586,14 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         // (out features); each half of the warps takes 32 of the columns
         if (quad < 2) {
             const int o = r;  // out feature
-            tmem_ld32(lb + CDW3, v);
+            tmem_ldw(lb + CDW3, v);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) atomicAdd(&grads[OW3 + o * HID + f0 + k], v[k]);
-            tmem_ld32(lb + CDW2, v);
+            for (int k = 0; k < FW; ++k) atomicAdd(&grads[OW3 + o * HID + f0 + k], v[k]);
+            tmem_ldw(lb + CDW2, v);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) atomicAdd(&grads[OW2 + o * HID + f0 + k], v[k]);
+            for (int k = 0; k < FW; ++k) atomicAdd(&grads[OW2 + o * HID + f0 + k], v[k]);
             if (hf == 0) {
-                tmem_ld32(lb + CDW1, v);  // the first 16 columns hold dW1
+                tmem_ldw(lb + CDW1, v);  // the first 16 columns hold dW1
 #pragma unroll
                 for (int k = 0; k < IN; ++k) atomicAdd(&grads[OW1 + o * IN + k], v[k]);
             }
