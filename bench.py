@@ -52,6 +52,8 @@ def parse():
                    help="2d: 4096^2 Moore (default line); 3d-cp: 512^3 plasticity-driven hybrid; ensemble: 256 "
                         "replicas; surrogate: 1024^3 plain vs surrogate time-to-texture")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--edge", type=int, default=None,
+                   help="3d-cp: lattice edge (default 512); grains scale with the volume")
     a = p.parse_args()
     if a.mcs is None:
         a.mcs = {"2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20, "texture2d": 1000,
@@ -456,6 +458,12 @@ def run_3d_cp(args):
     torch.cuda.set_device(0)
     Wc = synth.W3D_CP
     L, G, N = Wc.L, Wc.G, Wc.N
+    name = Wc.name
+    if args.edge and args.edge != L[0]:
+        e = int(args.edge)
+        L, N = (e, e, e), e ** 3
+        G = max(1, round(Wc.G * N / Wc.N))
+        name = f"3d-{e}-moore26-g{G}-cp"
     ex = Wc.extra
     lat = hm.Lattice(3, L, 26, 256, Wc.seed, G, hm.FIELD_POINT)
     q = torch.empty(N, dtype=torch.int32, device="cuda")
@@ -513,7 +521,7 @@ def run_3d_cp(args):
         "metric": "Potts site-updates/s", "value": round(N * args.mcs / tot, 1), "unit": "site-updates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot * 1e3, 2),
         "higher_is_better": True, "dtype": "int32 sweep / fp32+fp64 plasticity", "data": "synthetic",
-        "config": {"workload": Wc.name, "lattice": list(L), "grains": G, "kT": Wc.kT, "mcs": args.mcs,
+        "config": {"workload": name, "lattice": list(L), "grains": G, "kT": Wc.kT, "mcs": args.mcs,
                    "refresh": "MCP every 50 MCS, 2 increments of 1e-4", "tile": {"variant": int(chosen),
                    "ms_per_2_mcs": [round(float(x), 3) for x in ms]}},
         "sweep": {"site_updates_per_s": round(rate_sw, 1), "bytes_per_site_update": BYTES_3D_POINT,
