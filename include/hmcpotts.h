@@ -354,7 +354,8 @@ HP_API int hp_sur_generate(const hp_cp_params* prm, uint64_t seed, const float* 
  * = sigma_hat, gamma_hat): y = MLP(f(q_g), load), e_g = energy_scale (y0 w + y1 erho)
  * [J], b_g = round-half-even(256 e_g) clamped to +-2^20 into b_out (device
  * int32[G], the HP_FIELD_GRAIN table); e_out (device float[G]) may be NULL.
- * Synchronises `stream`.                                                     */
+ * Asynchronous on `stream`; the host load vector is read before the call
+ * returns and may be released at once.                                       */
 HP_API int hp_sur_field(const float* params, const float* quat, int32_t G, const float* load, const hp_sur_scales* sc,
                         double energy_scale, int32_t* b_out, float* e_out, void* stream);
 

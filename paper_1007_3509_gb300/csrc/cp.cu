@@ -144,7 +144,9 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
             Z += (double)wgt[al];
         }
         const uint4 u = draw(a.seed, (uint64_t)p, t, kTagMcp, 0);
-        const double Rn = (double)u.x * (1.0 / 4294967296.0);
+        // first a with R < sum_{b <= a} w_b / Z, tested as R Z < sum_{b <= a} w_b
+        // (no division per candidate; FP64 sums)
+        const double RZ = (double)u.x * (1.0 / 4294967296.0) * Z;
         double cum = 0.0;
         int pick = -1, last = -1;
         float tau_pick = 0.0f;
@@ -152,8 +154,8 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         for (int al = 0; al < 12; ++al) {
             if (!(mask >> al & 1)) continue;
             last = al;
-            cum += (double)wgt[al] / Z;
-            if (pick < 0 && Rn < cum) { pick = al; tau_pick = tau[al]; }
+            cum += (double)wgt[al];
+            if (pick < 0 && RZ < cum) { pick = al; tau_pick = tau[al]; }
         }
         if (pick < 0) {
             pick = last;

@@ -150,6 +150,8 @@ def run_surrogate(torch, cfg: HybridConfig, params, load_table, time_it=True):
             torch.cuda.synchronize()
         f0 = time.perf_counter()
         hm.hp_sur_field(params, quat, cfg.G, load_table[min(incr, len(load_table)) - 1], cfg.energy_scale, b)
+        if time_it:
+            torch.cuda.synchronize()
         t_field += time.perf_counter() - f0
         lat.hp_sweep(cfg.refresh_every)
     torch.cuda.synchronize()
