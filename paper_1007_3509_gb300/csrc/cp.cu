@@ -171,15 +171,18 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         if (!hard) {
             xs = (at - g0) / k;
         } else {
+            // Newton on the FP64 residual; the step uses an FP32 reciprocal of
+            // the slope (a relative step error near 1e-7 leaves the iteration
+            // converging to the same FP64 root, judged by the exact residual)
             const double sat = a.taus - g0;
-            xs = (at - g0) / (k + sat * hr);
+            xs = (at - g0) * (double)(1.0f / (float)(k + sat * hr));
 #pragma unroll 1
             for (int it = 0; it < 8; ++it) {
                 const double ey = exp_neg(hr * xs);
                 const double f = at - xs * k - (a.taus - sat * ey);
-                const double fp = -k - sat * hr * ey;
-                xs -= f / fp;
                 if (fabs(f) < 1e-13 * a.tau0) break;
+                const double fp = -k - sat * hr * ey;
+                xs -= f * (double)(1.0f / (float)fp);
             }
         }
         const float sg = tau_pick > 0.f ? 1.f : -1.f;
