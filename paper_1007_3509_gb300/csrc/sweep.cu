@@ -782,7 +782,7 @@ int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
 // (row-major window, persistent CTAs).  All give identical lattices; the
 // autotuner picks one.  TMA variants serve single lattices only.
 // Strip variants (strip.cu): one warp per strip, WX = 32 x columns per lane,
-// TY = most core rows per strip.  Tile variants (tile.cu): WX x (TY + 8)
+// TY = most core rows per strip.  Tile variants (tile.cu): WX x (TY + 4)
 // windows fed by bulk TMA copies.
 struct Variant {
     int WX, TY;
@@ -795,16 +795,19 @@ constexpr Variant kV2D[kVariants2D] = {
     {128, 64, false, false, false}, {128, 32, false, false, false}, {64, 64, false, false, false},
     {128, 32, true, false, false},  {128, 24, true, false, false},  {256, 16, false, true, false},
     {256, 32, false, true, false},  {128, 16, false, true, false},  {128, 32, false, true, false},
-    {128, 24, false, false, true},  {128, 56, false, false, true},  {64, 56, false, false, true}};
+    {128, 28, false, false, true},  {128, 60, false, false, true},  {64, 60, false, false, true}};
 constexpr Variant kV3D[kVariants3D] = {
     {128, 32, false, false, false}, {128, 16, false, false, false}, {64, 32, false, false, false},
     {64, 16, false, false, false},  {64, 32, true, false, false},   {64, 16, true, false, false},
     {64, 64, false, true, false},   {128, 64, false, true, false},  {64, 32, false, true, false},
-    {64, 56, false, false, true},   {64, 24, false, false, true},   {128, 24, false, false, true},
-    {64, 32, false, false, true}};
+    {64, 60, false, false, true},   {64, 28, false, false, true},   {128, 28, false, false, true},
+    {64, 36, false, false, true}};
 
 int n_variants(int nbr) { return nbr == 26 ? kVariants3D : (nbr == 6 ? 1 : kVariants2D); }
 Variant variant_of(int nbr, int v) { return nbr == 26 ? kV3D[v] : kV2D[v]; }
+// Window rows: tile windows carry two halo rows above and below the core, the
+// plane kernels four.
+int window_rows(const Variant& v) { return v.TY + (v.tile ? 4 : 8); }
 
 template <int NBR, int WX, int TY, int FIELD, bool HASMP>
 int launch_one(const PlaneArgs* a, const BatchArgs* b, int64_t blocks, int planes, cudaStream_t s) {
@@ -913,8 +916,9 @@ int launch_variant(int nbr, int v, int field, bool m, const PlaneArgs* a, const 
                    int planes, cudaStream_t s) {
     const Variant var = variant_of(nbr, v);
     if (var.tile) {
-        if (a) return blocks == 0 ? HP_OK : tile_launch(*a, field, m, nbr, planes, var.WX, var.TY + 8, s);
-        return tile_launch_batch(b->args, b->start, b->R, blocks, b->sweep_add, field, m, nbr, var.WX, var.TY + 8, s);
+        if (a) return blocks == 0 ? HP_OK : tile_launch(*a, field, m, nbr, planes, var.WX, window_rows(var), s);
+        return tile_launch_batch(b->args, b->start, b->R, blocks, b->sweep_add, field, m, nbr, var.WX,
+                                 window_rows(var), s);
     }
     if (var.strip) {
         if (!a) return set_error(HP_ERR_ARG, "sweep: strip variants serve single lattices only");
@@ -982,7 +986,7 @@ PlaneArgs plane_args(const hp_handle* h, int variant, const int32_t* q_in, const
     a.Lz = (int)h->lat.L[2];
     a.zpar = zpar;
     const Variant v = variant_of(h->lat.nbr, variant);
-    const int TX = v.WX - 8, WY = v.TY + 8;
+    const int TX = v.WX - 8, WY = window_rows(v);
     a.tiles_x = (a.Lx + TX - 1) / TX;
     a.tiles = a.tiles_x * ((a.Ly + v.TY - 1) / v.TY);
     a.fast = (a.Lx >= v.WX && a.Ly >= WY) ? 1 : 0;

@@ -1,8 +1,8 @@
 // Tile kernel: the fused checkerboard sweep (Eq. (7), Sec. 4) on a row-major
 // window in shared memory, built to spend few instructions per site.
 //
-// One CTA = one WX x WY window (a halo of four sites around a (WX-8) x (WY-8)
-// core) of one plane.  The window's rows arrive by bulk TMA copies
+// One CTA = one WX x WY window of one plane: a (WX-8) x (WY-4) core with a
+// halo of four columns and two rows.  The window's rows arrive by bulk TMA copies
 // (cp.async.bulk, one per row and array, a second one where a row crosses the
 // periodic x boundary; completion on one mbarrier with a clock-limited wait).
 // All colour phases that live in the plane then run in shared memory; in 3D
@@ -20,8 +20,15 @@
 //      proposals of another grain are compacted into a per-warp queue, and the
 //      warp then counts both grains among each one's neighbours and runs the
 //      Metropolis test with all lanes busy.
-// Columns and rows outside [p+1, W-p-1) are left alone in phase p; after the
-// last phase the core is exact and is written to the output buffer.
+// Phase p updates the columns [p+1, WX-p-1) and the rows [y_p, WY-y_p); after
+// the last phase the core is exact and is written to the output buffer.  The
+// halo follows from which earlier phases a phase reads.  Red/black: phase 1
+// reads phase 0 along x and y, so y_p = p + 1.  Four colours (x&1) + 2(y&1):
+// phase 1 reads phase 0 only along x; phase 2 reads phase 0 along y and phase
+// 1 diagonally; phase 3 reads phase 0 diagonally, phase 1 along y and phase 2
+// along x.  The exact region thus loses a column at every phase but a row only
+// at phases 0 and 2: y_p = 1 + p/2, two rows of halo (the four columns are
+// also what keeps every window row on a 16-byte boundary).
 #include "sweep.cuh"
 
 namespace hp {
@@ -33,16 +40,16 @@ __device__ int g_tile_err;
 template <int NBR, int WX, int WY, bool HASMP>
 struct TileCfg {
     static constexpr bool Z = NBR == 26;
-    static constexpr int H = 4, TX = WX - 2 * H, TY = WY - 2 * H;
+    static constexpr int HX = 4, HY = 2, TX = WX - 2 * HX, TY = WY - 2 * HY;
     static constexpr int ARR = 1 + (HASMP ? 1 : 0) + (Z ? 2 : 0);  // q, mp, q(z-1), q(z+1)
     static constexpr int A_MP = 1, A_LO = HASMP ? 2 : 1, A_HI = A_LO + 1;
     static constexpr int NP = NBR == 4 ? 2 : 4;
     static constexpr int PAD = 8;                  // ints of padding before and after each array
     static constexpr int AS = WX * WY + 2 * PAD;   // array stride in ints
-    static constexpr int QPR = WX / 4;             // quads per row
-    static constexpr int RPP = kTileThreads / QPR; // rows per pass of stage A
+    static constexpr int QPR = WX / 4;             // quads per row (a lane keeps its quad)
     static constexpr int QCAP = NBR == 4 ? (WX / 2) * WY : (WX / 2) * ((WY + 1) / 2);
-    static_assert(WX % 4 == 0 && (AS * 4) % 16 == 0 && kTileThreads % QPR == 0, "tile shape");
+    static_assert(WX % 4 == 0 && (AS * 4) % 16 == 0 && 32 % QPR == 0 && TY % 2 == 0, "tile shape");
+    __host__ __device__ static constexpr int ylo(int p) { return NBR == 4 ? p + 1 : 1 + (p >> 1); }
     static size_t smem() { return 128 + sizeof(int32_t) * ((size_t)ARR * AS + QCAP + 8) + sizeof(uint2) * 64 * (kTileThreads / 32); }
 };
 
@@ -65,7 +72,7 @@ struct Tile {
         return fast ? wrap1(x0 - 4 + col, a.Lx) : wrapi(x0 - 4 + col, a.Lx);
     }
     __device__ __forceinline__ int gy_of(int r) const {
-        return fast ? wrap1(y0 - 4 + r, a.Ly) : wrapi(y0 - 4 + r, a.Ly);
+        return fast ? wrap1(y0 - Cfg::HY + r, a.Ly) : wrapi(y0 - Cfg::HY + r, a.Ly);
     }
     __device__ __forceinline__ static void offs(int kp, int& dx, int& dy, int& dz) {
         if (NBR == 4) Geo<2, 4>::off(kp, dx, dy, dz);
@@ -145,7 +152,7 @@ template <int NBR, int WX, int WY, int FIELD, bool HASMP>
 __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, const int zidx, unsigned char* raw) {
     using T = Tile<NBR, WX, WY, FIELD, HASMP>;
     using Cfg = typename T::Cfg;
-    constexpr int ARR = Cfg::ARR, AS = Cfg::AS, PAD = Cfg::PAD, NP = Cfg::NP, QPR = Cfg::QPR, RPP = Cfg::RPP;
+    constexpr int ARR = Cfg::ARR, AS = Cfg::AS, PAD = Cfg::PAD, NP = Cfg::NP, QPR = Cfg::QPR;
     constexpr int M = NBR;
     constexpr bool Z = Cfg::Z;
     // rows by bulk TMA copies when a row of the window wraps at most once and
@@ -207,22 +214,22 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
     } else {
         for (int i = threadIdx.x; i < ARR * WY * WX; i += kTileThreads) {
             const int arr = i / (WY * WX), rem = i - arr * (WY * WX), r = rem / WX, c = rem - r * WX;
-            base[arr * AS + PAD + rem] = src(arr)[(int64_t)a.Lx * wrapi(t.y0 - 4 + r, a.Ly) + wrapi(t.x0 - 4 + c, a.Lx)];
+            base[arr * AS + PAD + rem] = src(arr)[(int64_t)a.Lx * wrapi(t.y0 - Cfg::HY + r, a.Ly) + wrapi(t.x0 - 4 + c, a.Lx)];
         }
         __syncthreads();
     }
 
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int qd = threadIdx.x % QPR, rs = threadIdx.x / QPR;
-    const int c0 = 4 * qd;
+    const int warp = (int)(threadIdx.x >> 5);
+    const int c0 = 4 * (lane % QPR);
     const uint32_t cz = Z ? 4u * (uint32_t)a.zpar : 0u;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const int lo = p + 1, hi = WX - p - 1, hiy = WY - p - 1;
+        const int lo = p + 1, hi = WX - p - 1, loy = Cfg::ylo(p), hiy = WY - loy;
         // ---- A: interior test, queue the rest ---------------------------------
         constexpr int RSTEP = NBR == 4 ? 1 : 2;
-        const int rstart = NBR == 4 ? lo : lo + ((lo ^ (p >> 1)) & 1);
+        const int rstart = NBR == 4 ? loy : loy + ((loy ^ (p >> 1)) & 1);
         // one quad of row r: sites ca = c0 + px and cb = ca + 2; bits 0/1 of
         // the result say which of them need the Metropolis stage
         auto item = [&](const int r, int& ca, int& cb) -> uint32_t {
@@ -273,9 +280,12 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
             cb = cb_;
             return (va && acc0 != 0u ? 1u : 0u) | (vb && acc1 != 0u ? 2u : 0u);
         };
-        // two rows per trip: their loads and shuffles overlap
-        for (int r0 = rstart; r0 < hiy; r0 += 2 * RSTEP * RPP) {
-            const int r1 = r0 + RSTEP * rs, r2 = r1 + RSTEP * RPP;
+        // the phase's (row, quad) items in chunks of 64, one chunk per warp
+        // trip, two items per lane whose loads and shuffles overlap; a lane
+        // keeps its quad, so both items and all chunks share its columns
+        const int nitems = (hiy - rstart + RSTEP - 1) / RSTEP * QPR;
+        for (int ch = warp; 64 * ch < nitems; ch += kTileThreads / 32) {
+            const int r1 = rstart + RSTEP * ((64 * ch + lane) / QPR), r2 = r1 + RSTEP * (32 / QPR);
             int ca1, cb1, ca2, cb2;
             const uint32_t f1 = item(r1, ca1, cb1);
             const uint32_t f2 = item(r2, ca2, cb2);
@@ -300,9 +310,9 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
         // proposals of another grain go to the warp's queue.  B2: the warp
         // tests them, all lanes busy.
         const int n = qn[p];
-        uint2* wq = wqueue + 64 * (threadIdx.x >> 5);
+        uint2* wq = wqueue + 64 * warp;
         for (int k0 = 0; k0 < n; k0 += 2 * kTileThreads) {
-            const int k1 = k0 + 64 * (int)(threadIdx.x >> 5) + lane, k2 = k1 + 32;
+            const int k1 = k0 + 64 * warp + lane, k2 = k1 + 32;
             uint2 w1 = make_uint2(0u, 0u), w2 = make_uint2(0u, 0u);
             const bool a1 = k1 < n && t.draw_site(queue[k1], colour, w1);
             const bool a2 = k2 < n && t.draw_site(queue[k2], colour, w2);
@@ -318,7 +328,7 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
     }
     (void)M;
 
-    // ---- write the core: rows [4, WY - 4), quads 1 .. QPR - 2 ----------------
+    // ---- write the core: rows [HY, WY - HY), quads 1 .. QPR - 2 --------------
     int32_t* qo = a.q_out + sxy * t.z;
     int32_t* mpo = HASMP ? a.mp_out + sxy * t.z : nullptr;
     constexpr int CQ = QPR - 2;
@@ -326,7 +336,7 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
         const int cy = i / CQ, qq = 1 + (i - cy * CQ);
         const int gx = t.x0 + 4 * (qq - 1), gy = t.y0 + cy;
         if (gx >= a.Lx || gy >= a.Ly) continue;
-        const int li = (cy + 4) * WX + 4 * qq;
+        const int li = (cy + Cfg::HY) * WX + 4 * qq;
         const int64_t o = gx + (int64_t)a.Lx * gy;
         if (a.vec) {
             *reinterpret_cast<int4*>(qo + o) = *reinterpret_cast<const int4*>(t.S + li);

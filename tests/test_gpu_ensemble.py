@@ -42,7 +42,9 @@ def _oracle_run(oracle, ref, n, sweep0=0):
 # interior tiles (TMA copies in the TMA-fed variants)
 VARIANT_GEOMS = [(2, (250, 140), 8), (2, (64, 70), 8), (2, (132, 96), 4), (2, (512, 200), 8), (2, (516, 132), 4),
                  (3, (136, 40, 8), 26), (3, (64, 34, 6), 26), (3, (12, 10, 4), 26), (3, (256, 96, 8), 26),
-                 (3, (200, 72, 6), 26)]
+                 (3, (200, 72, 6), 26),
+                 # whole numbers of tile cores (120 x 60 and 56 x 36): no ragged tile
+                 (2, (240, 120), 8), (3, (112, 72, 4), 26)]
 
 
 @pytest.mark.parametrize("dim,L,nbr", VARIANT_GEOMS)
