@@ -661,22 +661,28 @@ def run_texture(args):
     from paper_1007_3509_gb300 import build, texture
     build.build()
     torch.cuda.set_device(0)
+    # one untimed run of the same configuration first: the first run in a process
+    # also pays one-time start-up (module loading, first graph instantiation)
     if args.workload == "texture2d":
         sl = (0, args.mcs // 10, args.mcs // 3, args.mcs)
+        texture.run_gaussian_2d(torch, slices=(0, 10))
         r = texture.run_gaussian_2d(torch, slices=sl)
         low = list(range(0, 10)) + list(range(80, 90))
         print(json.dumps({"workload": "texture2d-gaussian-eq9-100x500^2", "slices": list(sl),
                           "mean_b_J": [round(x, 5) for x in r["mean_b"]],
                           "low_energy_fraction": [round(float(h[low].sum() / h.sum()), 4) for h in r["hist"]],
-                          "seconds": round(r["seconds"], 2),
+                          "seconds": round(r["seconds"], 3), "warmup": "one untimed run of 10 MCS",
+                          "timed": "sweeps + per-slice measurement of all 100 members",
                           "site_updates_per_s": round(100 * 500 * 500 * args.mcs / r["seconds"], 1)}))
     else:
         n_incr = max(1, args.mcs // 2)
-        r = texture.run_plastic_3d(torch, L=(256, 256, 256), G=32000, kT=1.0, n_incr=n_incr, mcs_per_incr=2,
-                                   e_incr=1e-4, energy_scale=200.0, every=max(1, n_incr // 10))
+        kw = dict(L=(256, 256, 256), G=32000, kT=1.0, mcs_per_incr=2, e_incr=1e-4, energy_scale=200.0)
+        texture.run_plastic_3d(torch, n_incr=2, every=1, **kw)
+        r = texture.run_plastic_3d(torch, n_incr=n_incr, every=max(1, n_incr // 10), **kw)
         print(json.dumps({"workload": "texture3d-plastic-zrot-256^3", "grains": 32000, "kT": 1.0,
                           "e_incr": 1e-4, "energy_scale": 200.0, "mcs": 2 * n_incr, "t": r["t"],
-                          "g_deg": [round(x, 3) for x in r["g"]], "seconds": round(r["seconds"], 2)}))
+                          "g_deg": [round(x, 3) for x in r["g"]], "seconds": round(r["seconds"], 3),
+                          "warmup": "one untimed run of 2 increments"}))
 
 
 def main():

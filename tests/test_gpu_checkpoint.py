@@ -1,5 +1,6 @@
 """Checkpoint / resume: a run split by save and load is bit-identical to the
-uninterrupted run and to the oracle; corrupted or mismatched files are refused."""
+uninterrupted run and to the oracle; corrupted, truncated, foreign or mismatched
+files are refused."""
 import numpy as np
 import pytest
 
@@ -55,6 +56,15 @@ def test_checkpoint_resume_bit_exact(oracle, tmp_path):
     with pytest.raises(hm.HPError) as e:
         b.hp_checkpoint_load(bad)
     assert e.value.code == hm.HP_ERR_CHECKSUM
+    # a truncated file and a file that is not a checkpoint are refused the same
+    # way, and a refused load leaves the handle as it was
+    for raw2 in (path.read_bytes()[:-7], b"not a checkpoint" * 8):
+        bad.write_bytes(raw2)
+        with pytest.raises(hm.HPError) as e:
+            b.hp_checkpoint_load(bad)
+        assert e.value.code == hm.HP_ERR_CHECKSUM
+    assert b.hp_get_sweep_counter() == 9
+    np.testing.assert_array_equal(b._bufs[0].cpu().numpy(), qa)
     # a checkpoint of another lattice is refused
     c = hm.Lattice(3, (8, 8, 8), 26, 256, 77, 5, hm.FIELD_POINT)
     qc = torch.zeros(512, dtype=torch.int32, device="cuda")
