@@ -130,7 +130,9 @@ HP_API int hp_init_voronoi_static(hp_handle* h, int32_t orient_kind, float* orie
 HP_API int hp_orientations(int32_t G, uint64_t seed, int32_t orient_kind, float* orient, void* stream);
 
 /* Stored-energy field table (borrowed device int32): G entries in
- * HP_FIELD_GRAIN mode, N entries (one per material point) in HP_FIELD_POINT. */
+ * HP_FIELD_GRAIN mode, N entries (one per material point) in HP_FIELD_POINT.
+ * HP_ERR_STATE for a HP_FIELD_NONE handle; HP_ERR_ARG when n is not G or N.
+ * Host-only bookkeeping: the table is read by the next sweep.                */
 HP_API int hp_set_field(hp_handle* h, const int32_t* table, int64_t n);
 
 /* Metropolis threshold table, host FP64 (Sec. 4, acceptance
@@ -177,6 +179,9 @@ HP_API int hp_sweep_autotune(hp_handle* h, int32_t n_mcs, float* ms_out, int32_t
  * since the last call gave up waiting for one of its copies; clears the flag. */
 HP_API int hp_sweep_status(int32_t* timed_out);
 
+/* The handle's MCS counter: the `sweep` word of the draws of the next MCS
+ * (Philox counter word 2).  Setting it replays or continues a run from any
+ * step; it takes effect at the next hp_sweep.  Host only; HP_ERR_ARG on NULL. */
 HP_API int hp_get_sweep_counter(const hp_handle* h, uint64_t* out);
 HP_API int hp_set_sweep_counter(hp_handle* h, uint64_t value);
 
@@ -243,7 +248,12 @@ typedef struct hp_ensemble hp_ensemble;
  * member keeps its own seed, sweep counter, temperature (threshold table) and
  * field.                                                                       */
 HP_API int hp_ensemble_create(hp_handle* const* members, int32_t R, hp_ensemble** out);
+/* Free the ensemble's graph, capture stream and device argument arrays; the
+ * members stay valid and belong to the caller.  Safe with NULL.              */
 HP_API int hp_ensemble_destroy(hp_ensemble* e);
+/* Tile variant used by hp_ensemble_sweep (default 0): plain plane tiles and
+ * lean tiles only; HP_ERR_ARG for TMA-fed plane tiles, strips or a variant
+ * not built for the members' field mode.                                     */
 HP_API int hp_ensemble_set_variant(hp_ensemble* e, int32_t v);
 /* Pick the fastest tile variant for the whole ensemble (state restored).      */
 HP_API int hp_ensemble_autotune(hp_ensemble* e, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream);
