@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         } else {
             // Newton on the FP64 residual; the step uses an FP32 reciprocal of
             // the slope (a relative step error near 1e-7 leaves the iteration
-            // converging to the same FP64 root, judged by the exact residual)
+            // converging to the same FP64 root, tested on the exact residual)
             const double sat = a.taus - g0;
             xs = (at - g0) * (double)(1.0f / (float)(k + sat * hr));
 #pragma unroll 1
