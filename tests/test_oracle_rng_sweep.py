@@ -331,6 +331,59 @@ def test_zero_coupling_zero_field(oracle, dim, L, nbr):
     assert set(np.unique(q1)) <= set(np.unique(q0))
 
 
+def _voter_mcs(oracle, L, nbr, seed, sweep, q):
+    """One MCS at J = 0, zero field, Metropolis (dE = 0 everywhere, thr[0] accepts):
+    every proposal is taken, so each site of colour c copies the neighbour its
+    draw picks -- a voter model.  Written from the stated conventions alone:
+    colours 0..C-1 in order (Sec. 4), neighbour k = (u0 M) >> 32 in the stated
+    order, draws keyed by (site lo, site hi, MCS, tag 0 << 24 | colour)."""
+    L3 = tuple(L) + (1,) * (3 - len(L))
+    Lx, Ly, Lz = L3
+    idx = np.arange(Lx * Ly * Lz, dtype=np.int64)
+    x, y, z = idx % Lx, (idx // Lx) % Ly, idx // (Lx * Ly)
+    if nbr == 4:
+        offs, col = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)], (x + y) % 2
+    elif nbr == 6:
+        offs, col = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)], (x + y + z) % 2
+    elif nbr == 8:
+        offs = [(dx, dy, 0) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+        col = x % 2 + 2 * (y % 2)
+    else:
+        offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy, dz) != (0, 0, 0)]
+        col = x % 2 + 2 * (y % 2) + 4 * (z % 2)
+    offs = np.array(offs, dtype=np.int64)
+    flips = 0
+    for c in range(int(col.max()) + 1):
+        sites = idx[col == c]
+        ctr = np.zeros((sites.size, 4), dtype=np.uint32)
+        ctr[:, 0] = sites & 0xFFFFFFFF
+        ctr[:, 1] = sites >> 32
+        ctr[:, 2] = sweep
+        ctr[:, 3] = c
+        u0 = oracle.philox(seed, ctr)[:, 0].astype(np.uint64)
+        k = ((u0 * np.uint64(len(offs))) >> np.uint64(32)).astype(np.int64)
+        o = offs[k]
+        nb = (x[sites] + o[:, 0]) % Lx + Lx * ((y[sites] + o[:, 1]) % Ly + Ly * ((z[sites] + o[:, 2]) % Lz))
+        new = q[nb]  # neighbours carry other colours: one simultaneous update
+        flips += int(np.count_nonzero(new != q[sites]))
+        q[sites] = new
+    return flips
+
+
+@pytest.mark.parametrize("dim,L,nbr", [(2, (16, 12), 4), (2, (12, 16), 8), (3, (8, 6, 4), 6), (3, (6, 8, 4), 26)])
+def test_zero_coupling_metropolis_is_a_voter_model(oracle, dim, L, nbr):
+    """J = 0, zero field, Metropolis: the oracle's lattice and flip count equal the
+    voter-model restatement bit for bit over several MCS (colour order, neighbour
+    order and draw keys all enter)."""
+    q0 = synth.random_lattice(L, 5, seed=3)
+    thr, D = oracle.threshold_table(0.7, zero_rule=0)
+    q, _, _, flips = oracle.sweep(dim, L, nbr, 0, 99, 5, 3, thr, D, q0)
+    ref = q0.astype(np.int64).copy()
+    ref_flips = sum(_voter_mcs(oracle, L, nbr, 99, 5 + t, ref) for t in range(3))
+    np.testing.assert_array_equal(q, ref)
+    assert flips == ref_flips > 0
+
+
 @pytest.mark.parametrize("dim,L,nbr", [(2, (16, 16), 4), (2, (16, 16), 8), (3, (8, 8, 8), 6), (3, (8, 8, 8), 26)])
 def test_flat_interface_frozen_at_zero_temperature(oracle, dim, L, nbr):
     """A flat boundary with zero field at kT = 0: every flip raises the energy, so nothing moves."""
