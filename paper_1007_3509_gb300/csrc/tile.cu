@@ -10,11 +10,13 @@
 // odd planes), exactly as in the plane kernel, and each MCS is two launches.
 //
 // Per phase:
-//   A. every thread takes one aligned quad of four columns in one row of the
-//      colour: one 128-bit and one 32-bit shared load per neighbour row give the
-//      two sites of the colour in the quad and all their neighbours; a site is
-//      interior when the OR of (neighbour XOR site) over its neighbourhood is
-//      zero.  The other sites go to a block-wide queue, one atomic per warp.
+//   A. the phase's (row, quad) items go out in chunks of 64 per warp trip, two
+//      per lane; a lane keeps one aligned quad of four columns.  One 128-bit
+//      shared load per neighbour row, with the edge columns taken from the
+//      neighbouring lanes by shuffle, gives the two sites of the colour in the
+//      quad and all their neighbours; a site is interior when the OR of
+//      (neighbour XOR site) over its neighbourhood is zero.  The other sites go
+//      to a block-wide queue, one atomic per warp.
 //   B. every queued site draws Philox and picks its neighbour (each thread
 //      takes two queue entries at once, so their Philox rounds overlap); the
 //      proposals of another grain are compacted into a per-warp queue, and the
