@@ -44,7 +44,9 @@ VARIANT_GEOMS = [(2, (250, 140), 8), (2, (64, 70), 8), (2, (132, 96), 4), (2, (5
                  (3, (136, 40, 8), 26), (3, (64, 34, 6), 26), (3, (12, 10, 4), 26), (3, (256, 96, 8), 26),
                  (3, (200, 72, 6), 26),
                  # whole numbers of tile cores (120 x 60 and 56 x 36): no ragged tile
-                 (2, (240, 120), 8), (3, (112, 72, 4), 26)]
+                 (2, (240, 120), 8), (3, (112, 72, 4), 26),
+                 # lattices smaller than any window: every window row and column wraps
+                 (2, (4, 4), 8), (2, (4, 4), 4), (2, (2, 6), 4), (2, (66, 2), 8)]
 
 
 @pytest.mark.parametrize("dim,L,nbr", VARIANT_GEOMS)
