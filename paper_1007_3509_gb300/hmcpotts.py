@@ -2,7 +2,9 @@
 
 Argument marshalling only: every computation runs in the library's CUDA
 kernels.  Device buffers are torch CUDA tensors (their ``data_ptr()`` is passed
-through); streams default to torch's current stream.  If the shared library
+through, after a check that each is a contiguous CUDA tensor of the element
+size and at least the length the call reads or writes, since the C ABI cannot
+see sizes); streams default to torch's current stream.  If the shared library
 has not been built, every call raises instead of falling back to anything.
 """
 from __future__ import annotations
@@ -128,12 +130,32 @@ def _check(rc):
         raise HPError(rc, lib().hp_last_error_message().decode())
 
 
-def _ptr(t):
-    if t is None:
-        return None
-    if isinstance(t, int):
+def _dev(t, n, itemsize, what):
+    """Device pointer of a buffer the library reads or writes n elements of.
+
+    The C ABI takes raw pointers and cannot see sizes, so a torch tensor is
+    checked here: on a CUDA device, contiguous, of the element size the call
+    expects, and holding at least n elements.  None passes through (optional
+    buffers) and so does an int (a raw device pointer the caller vouches for).
+    """
+    if t is None or isinstance(t, int):
         return t
+    bad = None
+    if not getattr(t, "is_cuda", False):
+        bad = "needs a CUDA tensor"
+    elif not t.is_contiguous():
+        bad = "needs a contiguous tensor"
+    elif t.element_size() != itemsize:
+        bad = f"needs {itemsize}-byte elements, got {t.dtype}"
+    elif t.numel() < n:
+        bad = f"needs at least {n} elements, got {t.numel()}"
+    if bad:
+        raise HPError(HP_ERR_ARG, f"{what}: {bad}")
     return t.data_ptr()
+
+
+def _orient_len(kind, G):
+    return G if kind == ORIENT_ANGLE else 4 * G
 
 
 def _stream(stream):
@@ -164,23 +186,30 @@ def hp_build_threshold_table(kT: float, zero_rule: int = 0, cap: int = 1 << 16):
 
 
 def hp_orientations(G, seed, kind, orient, stream=None):
-    _check(lib().hp_orientations(int(G), C.c_uint64(seed), int(kind), _ptr(orient), _stream(stream)))
+    o = _dev(orient, _orient_len(kind, G), 4, "hp_orientations orient")
+    _check(lib().hp_orientations(int(G), C.c_uint64(seed), int(kind), o, _stream(stream)))
 
 
 def hp_grain_field(quat, C11, C12, C44, sigma, k_disl, energy_scale, b_out, w_out=None, mmax_out=None,
                    stream=None):
     G = quat.shape[0]
-    _check(lib().hp_grain_field(int(G), _ptr(quat), C11, C12, C44, sigma, k_disl, energy_scale, _ptr(b_out),
-                                _ptr(w_out), _ptr(mmax_out), _stream(stream)))
+    w = "hp_grain_field"
+    _check(lib().hp_grain_field(int(G), _dev(quat, 4 * G, 4, w + " quat"), C11, C12, C44, sigma, k_disl,
+                                energy_scale, _dev(b_out, G, 4, w + " b_out"), _dev(w_out, G, 4, w + " w_out"),
+                                _dev(mmax_out, G, 4, w + " mmax_out"), _stream(stream)))
 
 
 def hp_texture(G, kind, orient, counts, bins, hist, stream=None):
-    _check(lib().hp_texture(int(G), int(kind), _ptr(orient), _ptr(counts), _ptr(bins), _ptr(hist),
-                            _stream(stream)))
+    so3 = kind == ORIENT_SO3
+    w = "hp_texture"
+    _check(lib().hp_texture(int(G), int(kind), _dev(orient, _orient_len(kind, G), 4, w + " orient"),
+                            _dev(counts, G, 8, w + " counts"), _dev(bins, 2 * G if so3 else G, 4, w + " bins"),
+                            _dev(hist, 24 if so3 else 90, 8, w + " hist"), _stream(stream)))
 
 
 def hp_gaussian_field(G, angle, scale, b_out, stream=None):
-    _check(lib().hp_gaussian_field(int(G), _ptr(angle), float(scale), _ptr(b_out), _stream(stream)))
+    _check(lib().hp_gaussian_field(int(G), _dev(angle, G, 4, "hp_gaussian_field angle"), float(scale),
+                                   _dev(b_out, G, 4, "hp_gaussian_field b_out"), _stream(stream)))
 
 
 def hp_texture_fit(hist):
@@ -193,26 +222,39 @@ def hp_texture_fit(hist):
 
 def hp_philox(seed, ctr, out, stream=None):
     n = ctr.numel() // 4
-    _check(lib().hp_philox(C.c_uint64(seed), _ptr(ctr), n, _ptr(out), _stream(stream)))
+    _check(lib().hp_philox(C.c_uint64(seed), _dev(ctr, 4 * n, 4, "hp_philox ctr"), n,
+                           _dev(out, 4 * n, 4, "hp_philox out"), _stream(stream)))
+
+
+_param_count = None
 
 
 def hp_mlp_param_count():
-    n = C.c_int64(0)
-    _check(lib().hp_mlp_param_count(C.byref(n)))
-    return n.value
+    global _param_count
+    if _param_count is None:
+        n = C.c_int64(0)
+        _check(lib().hp_mlp_param_count(C.byref(n)))
+        _param_count = n.value
+    return _param_count
 
 
 def hp_mlp_forward(params, X, Y, stream=None):
-    _check(lib().hp_mlp_forward(_ptr(params), _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
+    M, P, w = int(X.shape[0]), hp_mlp_param_count(), "hp_mlp_forward"
+    _check(lib().hp_mlp_forward(_dev(params, P, 4, w + " params"), _dev(X, 11 * M, 4, w + " X"), M,
+                                _dev(Y, 2 * M, 4, w + " Y"), _stream(stream)))
 
 
 def hp_mlp_gradients(params, X, T, grads, loss=None, stream=None):
-    _check(lib().hp_mlp_gradients(_ptr(params), _ptr(X), _ptr(T), int(X.shape[0]), _ptr(grads), _ptr(loss),
-                                  _stream(stream)))
+    M, P, w = int(X.shape[0]), hp_mlp_param_count(), "hp_mlp_gradients"
+    _check(lib().hp_mlp_gradients(_dev(params, P, 4, w + " params"), _dev(X, 11 * M, 4, w + " X"),
+                                  _dev(T, 2 * M, 4, w + " T"), M, _dev(grads, P, 4, w + " grads"),
+                                  _dev(loss, 1, 4, w + " loss"), _stream(stream)))
 
 
 def hp_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-    _check(lib().hp_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step), float(lr), float(beta1),
+    P, w = hp_mlp_param_count(), "hp_mlp_adam"
+    _check(lib().hp_mlp_adam(_dev(params, P, 4, w + " params"), _dev(grads, P, 4, w + " grads"),
+                             _dev(m, P, 4, w + " m"), _dev(v, P, 4, w + " v"), int(step), float(lr), float(beta1),
                              float(beta2), float(eps), _stream(stream)))
 
 
@@ -226,14 +268,23 @@ SUR_SCALES = hp_sur_scales(100.0, 1e-3, 0.01, 0.002)
 
 
 def hp_sur_generate(prm, seed, quat, n_orient, K, n_incr, X, Y, load_out=None, scales=SUR_SCALES, stream=None):
-    _check(lib().hp_sur_generate(C.byref(prm), C.c_uint64(seed), _ptr(quat), int(n_orient), int(K), int(n_incr),
-                                 C.byref(scales), _ptr(X), _ptr(Y), _ptr(load_out), _stream(stream)))
+    rows, w = int(n_orient) * int(n_incr), "hp_sur_generate"
+    _check(lib().hp_sur_generate(C.byref(prm), C.c_uint64(seed), _dev(quat, 4 * int(n_orient), 4, w + " quat"),
+                                 int(n_orient), int(K), int(n_incr), C.byref(scales), _dev(X, 11 * rows, 4, w + " X"),
+                                 _dev(Y, 2 * rows, 4, w + " Y"), _dev(load_out, 7 * int(n_incr), 4, w + " load_out"),
+                                 _stream(stream)))
 
 
 def hp_sur_field(params, quat, G, load, energy_scale, b_out, e_out=None, scales=SUR_SCALES, stream=None):
     ld = np.ascontiguousarray(load, dtype=np.float32)
-    _check(lib().hp_sur_field(_ptr(params), _ptr(quat), int(G), ld.ctypes.data, C.byref(scales),
-                              float(energy_scale), _ptr(b_out), _ptr(e_out), _stream(stream)))
+    if ld.size != 7:
+        raise HPError(HP_ERR_ARG, "hp_sur_field: load needs 7 values (stress, slip)")
+    w = "hp_sur_field"
+    _check(lib().hp_sur_field(_dev(params, hp_mlp_param_count(), 4, w + " params"), _dev(quat, 4 * int(G), 4,
+                                                                                         w + " quat"),
+                              int(G), ld.ctypes.data, C.byref(scales), float(energy_scale),
+                              _dev(b_out, int(G), 4, w + " b_out"), _dev(e_out, int(G), 4, w + " e_out"),
+                              _stream(stream)))
 
 
 def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=None, w_weight=1.0):
@@ -243,15 +294,21 @@ def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=N
 
 
 def hp_cp_reset(prm, P, eps_p, gamma, g, stream=None):
-    st = hp_cp_state(int(P), _ptr(eps_p), _ptr(gamma), _ptr(g))
+    P, w = int(P), "hp_cp_reset"
+    st = hp_cp_state(P, _dev(eps_p, 6 * P, 4, w + " eps_p"), _dev(gamma, P, 4, w + " gamma"),
+                     _dev(g, P, 4, w + " g"))
     _check(lib().hp_cp_reset(C.byref(prm), C.byref(st), _stream(stream)))
 
 
 def hp_cp_step(prm, seed, grain, quat, t0, n_incr, eps_p, gamma, g, sigma=None, w=None, erho=None, b=None,
                stream=None):
-    st = hp_cp_state(int(grain.numel()), _ptr(eps_p), _ptr(gamma), _ptr(g))
-    _check(lib().hp_cp_step(C.byref(prm), C.c_uint64(seed), _ptr(grain), _ptr(quat), C.c_uint32(t0), int(n_incr),
-                            C.byref(st), _ptr(sigma), _ptr(w), _ptr(erho), _ptr(b), _stream(stream)))
+    P, wh = int(grain.numel()), "hp_cp_step"
+    st = hp_cp_state(P, _dev(eps_p, 6 * P, 4, wh + " eps_p"), _dev(gamma, P, 4, wh + " gamma"),
+                     _dev(g, P, 4, wh + " g"))
+    _check(lib().hp_cp_step(C.byref(prm), C.c_uint64(seed), _dev(grain, P, 4, wh + " grain"),
+                            _dev(quat, 0, 4, wh + " quat"), C.c_uint32(t0), int(n_incr), C.byref(st),
+                            _dev(sigma, 6 * P, 4, wh + " sigma"), _dev(w, P, 4, wh + " w"),
+                            _dev(erho, P, 4, wh + " erho"), _dev(b, P, 4, wh + " b"), _stream(stream)))
 
 
 def hp_sweep_status():
@@ -328,19 +385,24 @@ class Lattice:
             pass
 
     def hp_bind(self, q, mp=None):
-        _check(lib().hp_bind(self._h, _ptr(q), _ptr(mp)))
+        _check(lib().hp_bind(self._h, _dev(q, self.N, 4, "hp_bind q"), _dev(mp, self.N, 4, "hp_bind mp")))
         self._keep = [q, mp]
 
+    def _voronoi_out(self, orient_kind, orient, seed_pos, w):
+        G = self.n_grains
+        return (_dev(orient, _orient_len(orient_kind, G), 4, w + " orient"), _dev(seed_pos, G, 8, w + " seed_pos"))
+
     def hp_init_voronoi(self, orient_kind=ORIENT_ANGLE, orient=None, seed_pos=None, stream=None):
-        _check(lib().hp_init_voronoi(self._h, int(orient_kind), _ptr(orient), _ptr(seed_pos), _stream(stream)))
+        o, sp = self._voronoi_out(orient_kind, orient, seed_pos, "hp_init_voronoi")
+        _check(lib().hp_init_voronoi(self._h, int(orient_kind), o, sp, _stream(stream)))
 
     def hp_init_voronoi_static(self, orient_kind=ORIENT_ANGLE, orient=None, seed_pos=None, stream=None):
         """Same as hp_init_voronoi, with no device allocation (fixed-size static scratch)."""
-        _check(lib().hp_init_voronoi_static(self._h, int(orient_kind), _ptr(orient), _ptr(seed_pos),
-                                            _stream(stream)))
+        o, sp = self._voronoi_out(orient_kind, orient, seed_pos, "hp_init_voronoi_static")
+        _check(lib().hp_init_voronoi_static(self._h, int(orient_kind), o, sp, _stream(stream)))
 
     def hp_set_field(self, table):
-        _check(lib().hp_set_field(self._h, _ptr(table), int(table.numel())))
+        _check(lib().hp_set_field(self._h, _dev(table, 0, 4, "hp_set_field table"), int(table.numel())))
         self._table = table
 
     def hp_set_threshold_table(self, thr, D, stream=None):
@@ -379,4 +441,5 @@ class Lattice:
         _check(lib().hp_checkpoint_load(self._h, str(path).encode(), _stream(stream)))
 
     def hp_grain_counts(self, counts, alive=None, stream=None):
-        _check(lib().hp_grain_counts(self._h, _ptr(counts), _ptr(alive), _stream(stream)))
+        _check(lib().hp_grain_counts(self._h, _dev(counts, self.n_grains, 8, "hp_grain_counts counts"),
+                                     _dev(alive, 1, 4, "hp_grain_counts alive"), _stream(stream)))
