@@ -10,10 +10,12 @@ producer by a small multilayer perceptron evaluated once per grain:
     x (11) -> GELU(W1 x + b1) (64) -> GELU(W2 . + b2) (64)
            -> GELU(W3 . + b3) (64) -> W4 . + b4 (2)
 
-with GELU(z) = z/2 (1 + erf(z / sqrt 2)) (exact erf).  Inputs are the grain
-quaternion (4), the macroscopic sample-frame stress of the load step (6) and
-the applied strain level (1), standardised; outputs are the standardised
-(w, E_rho).  Training minimises the mean squared error
+with GELU(z) = z/2 (1 + erf(z / sqrt 2)) (exact erf).  The 11 inputs are four
+cubic invariants of the grain's loading axis d = R^T e_x (|d| sorted
+decreasingly and d1^2 d2^2 + d2^2 d3^2 + d3^2 d1^2; ``oracle.surrogate``), the
+six components of the population-average sample-frame stress of the load
+step and the average accumulated slip, each divided by a fixed scale; the two
+outputs are (w, E_rho), each divided by a fixed scale.  Training minimises the mean squared error
 L = 1/(2B) sum_b sum_o (y_bo - t_bo)^2 with Adam (Kingma & Ba, 2015):
 m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
 theta <- theta - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).

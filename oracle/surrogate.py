@@ -22,12 +22,28 @@ import oracle
 
 
 def orientation_features(quat):
+    """Four cubic invariants of the loading axis d = R(q)^T e_x, one row per
+    quaternion (w, x, y, z): |d| sorted decreasingly and
+    d1^2 d2^2 + d2^2 d3^2 + d3^2 d1^2.  Row 0 of R is R^T e_x."""
     q = np.asarray(quat, dtype=np.float64)
     q = q / np.linalg.norm(q, axis=1, keepdims=True)
     R = Rotation.from_quat(np.stack([q[:, 1], q[:, 2], q[:, 3], q[:, 0]], axis=1)).as_matrix()
     a = -np.sort(-np.abs(R[:, 0, :]), axis=1)
     inv4 = (a[:, 0] * a[:, 1]) ** 2 + (a[:, 1] * a[:, 2]) ** 2 + (a[:, 2] * a[:, 0]) ** 2
     return np.concatenate([a, inv4[:, None]], axis=1)
+
+
+def sample_frame_stress(R, sigma_crystal):
+    """Crystal-frame stresses (Voigt order xx yy zz yz xz xy, [n, 6]) rotated
+    into the sample frame, R sigma R^T ([n, 3, 3]); R [n, 3, 3] maps crystal
+    vectors to sample vectors (the rotation of the orientation quaternion)."""
+    sg = np.asarray(sigma_crystal, dtype=np.float64)
+    S = np.zeros((sg.shape[0], 3, 3))
+    S[:, 0, 0], S[:, 1, 1], S[:, 2, 2] = sg[:, 0], sg[:, 1], sg[:, 2]
+    S[:, 1, 2] = S[:, 2, 1] = sg[:, 3]
+    S[:, 0, 2] = S[:, 2, 0] = sg[:, 4]
+    S[:, 0, 1] = S[:, 1, 0] = sg[:, 5]
+    return np.einsum("pik,pkl,pjl->pij", R, S, R)
 
 
 def samples(P, seed, quat, K, n_incr, scales):
@@ -49,12 +65,7 @@ def samples(P, seed, quat, K, n_incr, scales):
         ep, gm, sg, nR, nT = oracle.mcp_run(P, seed, grain, quat, t - 1, 1, ep, gm)
         near |= ((nR < 1e-5) | (nT < 1e-5)).reshape(n_orient, K).any(axis=1)
         w, er = oracle.mcp_energies(P, sg, gm)
-        S = np.zeros((npts, 3, 3))
-        S[:, 0, 0], S[:, 1, 1], S[:, 2, 2] = sg[:, 0], sg[:, 1], sg[:, 2]
-        S[:, 1, 2] = S[:, 2, 1] = sg[:, 3]
-        S[:, 0, 2] = S[:, 2, 0] = sg[:, 4]
-        S[:, 0, 1] = S[:, 1, 0] = sg[:, 5]
-        Ss = np.einsum("pik,pkl,pjl->pij", R, S, R)
+        Ss = sample_frame_stress(R, sg)
         sh = np.array([Ss[:, 0, 0].mean(), Ss[:, 1, 1].mean(), Ss[:, 2, 2].mean(), Ss[:, 1, 2].mean(),
                        Ss[:, 0, 2].mean(), Ss[:, 0, 1].mean()])
         gh = gm.mean()
