@@ -77,6 +77,12 @@ typedef struct hp_handle hp_handle;
 /* Latest error message of this thread (never NULL). */
 HP_API const char* hp_last_error_message(void);
 
+/* Copy this thread's latest error message into buf (capacity n bytes, always
+ * NUL-terminated, truncated if longer).  Messages are kept per host thread, so
+ * h may be NULL.  HP_ERR_ARG (without touching the message) if buf is NULL or
+ * n is 0.                                                                    */
+HP_API int hp_last_error(const hp_handle* h, char* buf, size_t n);
+
 /* Library build/version string (never NULL). */
 HP_API const char* hp_version(void);
 
@@ -97,6 +103,18 @@ HP_API int hp_destroy(hp_handle* h);
  * double-buffer copies (same sizes) used by the fused sweep.                  */
 HP_API int hp_bind(hp_handle* h, int32_t* q, int32_t* mp);
 
+/* Lattice state in and out (Sec. 4: the Potts spins q_i and, Sec. 6, the
+ * material point each site carries).  hp_set_spins copies N ids into the bound
+ * q (and N material-point indices into the bound mp when mp is not NULL) from
+ * host memory (is_host != 0; pinned memory makes the copy asynchronous) or
+ * from device memory; hp_get_spins copies them out the same way.  Ids are not
+ * checked here: a lattice holding ids outside 0..G-1 is reported by
+ * hp_grain_counts / hp_measure, and the sweep clamps every table index.
+ * HP_ERR_STATE if nothing is bound (or mp is given but no mp buffer is bound).
+ * Asynchronous on `stream`: host buffers must stay valid until it completes. */
+HP_API int hp_set_spins(hp_handle* h, const int32_t* q, const int32_t* mp, int32_t is_host, void* stream);
+HP_API int hp_get_spins(const hp_handle* h, int32_t* q, int32_t* mp, int32_t is_host, void* stream);
+
 /* Initial polycrystal (Sec. 4-5 set-up): Voronoi tessellation of G seeds.
  * Seeds are drawn in rounds from Philox(seed; g, round, tag 2 | 0); a site
  * drawn by several seeds goes to the lowest g, losers redraw.  Every site gets
@@ -116,12 +134,13 @@ HP_API int hp_init_voronoi(hp_handle* h, int32_t orient_kind, float* orient, int
  * Scratch (seed coordinates, cell lists and counters) lives in one file-scope
  * device array of HP_VORONOI_STATIC_BYTES (16 MiB) that every GPU loading the
  * library holds until exit; G above HP_VORONOI_STATIC_MAX_GRAINS is rejected
- * with HP_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array and each
- * call clears what it needs, so calls that overlap on the GPU (concurrent
- * streams, several host threads) race and must be serialised by the caller.
- * Like hp_init_voronoi it synchronises `stream` once per seeding round.       */
+ * with HP_ERR_ARG.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device.  The call reads a counter back
+ * to the host and synchronises `stream` once per seeding round, so it must
+ * never be made while the stream is being captured into a CUDA graph.  All
+ * calls share the one array and each call clears what it needs, so calls that
+ * overlap on the GPU (concurrent streams, several host threads) race and must
+ * be serialised by the caller.                                               */
 #define HP_VORONOI_STATIC_BYTES (16u << 20)
 #define HP_VORONOI_STATIC_MAX_GRAINS 262144
 HP_API int hp_init_voronoi_static(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, void* stream);
@@ -175,9 +194,24 @@ HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
 HP_API int hp_sweep_variants(int32_t nbr, int32_t* n);
 HP_API int hp_set_sweep_variant(hp_handle* h, int32_t v);
 HP_API int hp_sweep_autotune(hp_handle* h, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream);
-/* Synchronous: HP_ERR_TIMEOUT (and *timed_out = 1) if a TMA-fed sweep kernel
- * since the last call gave up waiting for one of its copies; clears the flag. */
+/* Synchronous: HP_ERR_TIMEOUT if a TMA-fed sweep kernel since the last call
+ * gave up waiting for one of its window copies (every such wait is bounded, about
+ * two seconds); clears the flag.  *timed_out = 1: the block then waited up to
+ * four more limits for the copies in flight and they landed before it left (the
+ * lattice written by that launch is wrong, the context is sound); 2: even that
+ * drain ran out, copies may have landed after the block left and the CUDA
+ * context should not be trusted further.  0 and HP_OK otherwise.             */
 HP_API int hp_sweep_status(int32_t* timed_out);
+
+/* Test hook of the timeout paths, no counterpart in the paper: one block waits
+ * on an mbarrier with nothing in flight (no copy or tensor-core operation) and
+ * a limit of limit_cycles (1 .. 2^32 SM clocks).  The one arrival it expects
+ * comes after two limits when late != 0 (the first wait gives up, the drain
+ * sees the arrival: flag 1) or never (the drain runs out too: flag 2).  The
+ * flag is raised exactly as by a sweep (unit 0, read by hp_sweep_status) or
+ * surrogate (unit 1, hp_mlp_status) kernel that timed out; since nothing was in
+ * flight, the context stays sound either way.  Asynchronous on `stream`.     */
+HP_API int hp_debug_wait_timeout(int32_t unit, int64_t limit_cycles, int32_t late, void* stream);
 
 /* The handle's MCS counter: the `sweep` word of the draws of the next MCS
  * (Philox counter word 2).  Setting it replays or continues a run from any
@@ -199,6 +233,35 @@ HP_API int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, void* 
  * rotation angle 2 atan2(z, w); bins int32[G]; hist int64[90].               */
 HP_API int hp_texture(int32_t G, int32_t orient_kind, const float* orient, const int64_t* counts, int32_t* bins,
                int64_t* hist, void* stream);
+
+/* One synchronous measurement of a bound lattice (Sec. 4 average grain size
+ * N / (grains alive); Sec. 5 texture and the bulk energy the grains carry).
+ * With accumulate = 0 the stats (and hist) are reset first; with accumulate
+ * != 0 this lattice's sums are added to them, so one struct can gather an
+ * ensemble of lattices.  Integer sums are exact; the derived doubles are
+ * recomputed from the accumulated sums on every call.                        */
+typedef struct {
+    int64_t sites;      /* sites measured                                       */
+    int64_t alive;      /* grains with at least one site (summed over lattices) */
+    double mean_area;   /* sites / alive: average grain size in sites            */
+    int64_t field_sum;  /* sum over sites of the field b_i (fixed point, 256 = 1 J):
+                           table[q_i] (HP_FIELD_GRAIN), table[mp_i] (HP_FIELD_POINT),
+                           0 (HP_FIELD_NONE)                                      */
+    double mean_field;  /* field_sum / 256 / sites: volume-weighted bulk energy [J] */
+    int64_t hist_total; /* sites in the texture histogram (its first block)       */
+    double families[4]; /* HP_ORIENT_SO3: volume fractions with no family, <100>,
+                           <110>, <111> within 15 degrees of the loading axis x   */
+    double mean_mmax;   /* HP_ORIENT_SO3: volume-weighted mean max Schmid factor
+                           from the 20 bin centres                                */
+} hp_stats;
+/* orient (device, as for hp_texture; NULL skips the texture): the histogram of
+ * hp_texture (24 bins for HP_ORIENT_SO3, 90 otherwise) is added into hist
+ * (host int64[n_bins], may be NULL).  Device scratch for the counts, bins and
+ * histogram is allocated on the first call and kept by the handle.  Returns
+ * HP_ERR_STATE if the lattice holds ids outside 0..G-1 (stats untouched), if
+ * nothing is bound, or if the handle's field table is not set.              */
+HP_API int hp_measure(hp_handle* h, int32_t orient_kind, const float* orient, int32_t accumulate, hp_stats* stats,
+                      int64_t* hist, int32_t n_bins, void* stream);
 
 /* Orientation-dependent Gaussian bulk energy of Eq. (9) (Sec. 5, Fig. 3): a
  * grain with angle t (device float[G], HP_ORIENT_ANGLE) has orientation
@@ -329,9 +392,11 @@ HP_API int hp_mlp_gradients(const float* params, const float* X, const float* T,
  * [param_count]) are the moment estimates, step counts from 1.               */
 HP_API int hp_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr, float beta1,
                        float beta2, float eps, void* stream);
-/* Synchronous: HP_ERR_TIMEOUT (and *timed_out = 1) if any surrogate kernel
- * since the last call gave up waiting for its tensor-core operations; clears
- * the flag.                                                                  */
+/* Synchronous: HP_ERR_TIMEOUT if any surrogate kernel since the last call gave
+ * up waiting for its tensor-core operations (bounded, about two seconds);
+ * clears the flag.  *timed_out = 1: the block then waited up to four more
+ * limits for the pending commit before freeing its tensor memory; 2: that
+ * drain ran out too and the context should not be trusted.                  */
 HP_API int hp_mlp_status(int32_t* timed_out);
 
 /* Fixed normalisation of the surrogate's inputs and targets.                  */
@@ -360,6 +425,31 @@ typedef struct {
 HP_API int hp_sur_generate(const hp_cp_params* prm, uint64_t seed, const float* quat, int32_t n_orient, int32_t K,
                            int32_t n_incr, const hp_sur_scales* sc, float* X, float* Y, float* load_out,
                            void* stream);
+/* Training of the surrogate on data of hp_sur_generate: `steps` Adam steps
+ * (hp_mlp_adam, step numbers step0 + 1 .. step0 + steps) on the loss of
+ * hp_mlp_gradients over minibatches of `batch` rows (rounded down to whole
+ * groups of `group` consecutive rows; 0 = every row) taken in turn from the
+ * start of X (device float[M][11]) and Y (device float[M][2]); the learning
+ * rate decays from lr to lr_floor * lr by a half cosine over the run:
+ *   lr_t = lr (lr_floor + (1 - lr_floor) (1 + cos(pi t / steps)) / 2).
+ * params, m, v: device float[hp_mlp_param_count()], updated in place.  loss
+ * (device float, may be NULL) receives the last minibatch loss; with
+ * log_every > 0 the loss after every log_every-th step is also copied to the
+ * host array loss_log[steps / log_every] (one synchronisation each).
+ * Allocates its gradient buffer for the duration of the call; asynchronous
+ * otherwise.                                                                  */
+typedef struct {
+    int32_t steps;    /* Adam steps                                           */
+    int64_t batch;    /* rows per minibatch (0 = all rows)                    */
+    int32_t group;    /* rows per group: minibatches hold whole groups        */
+    float lr;         /* initial learning rate                                */
+    float lr_floor;   /* final learning rate as a fraction of lr, in [0, 1]   */
+    float beta1, beta2, eps; /* Adam constants                                */
+    int32_t log_every;/* 0: no loss log                                       */
+} hp_sur_train_params;
+HP_API int hp_sur_train(float* params, float* m, float* v, const float* X, const float* Y, int64_t M,
+                        const hp_sur_train_params* tp, int32_t step0, float* loss, float* loss_log, void* stream);
+
 /* Per-grain driving field from the surrogate at one load state (host float[7]
  * = sigma_hat, gamma_hat): y = MLP(f(q_g), load), e_g = energy_scale (y0 w + y1 erho)
  * [J], b_g = round-half-even(256 e_g) clamped to +-2^20 into b_out (device

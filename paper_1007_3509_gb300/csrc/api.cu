@@ -49,6 +49,15 @@ using namespace hp;
 
 extern "C" const char* hp_last_error_message(void) { return g_last_error.c_str(); }
 
+extern "C" int hp_last_error(const hp_handle* h, char* buf, size_t n) {
+    (void)h;  // messages are kept per host thread, not per handle
+    if (!buf || n == 0) return HP_ERR_ARG;
+    const size_t k = g_last_error.size() < n - 1 ? g_last_error.size() : n - 1;
+    memcpy(buf, g_last_error.data(), k);
+    buf[k] = '\0';
+    return HP_OK;
+}
+
 extern "C" const char* hp_version(void) { return "hmcpotts 0.1 sm_103a"; }
 
 extern "C" int hp_kernel_launches(uint64_t* out) {
@@ -91,6 +100,9 @@ extern "C" int hp_destroy(hp_handle* h) {
     cudaFree(h->q_alt);
     cudaFree(h->mp_alt);
     cudaFree(h->thr);
+    cudaFree(h->m_counts);
+    cudaFree(h->m_bins);
+    cudaFree(h->m_small);
     delete h;
     return HP_OK;
 }
@@ -104,6 +116,32 @@ extern "C" int hp_bind(hp_handle* h, int32_t* q, int32_t* mp) {
     if (mp && !h->mp_alt) HP_CUDA(cudaMalloc((void**)&h->mp_alt, bytes));
     h->q = q;
     h->mp = mp;
+    return HP_OK;
+}
+
+// Upload (is_host != 0: from pageable or pinned host memory) or take from
+// device memory the lattice state q (and mp) of a bound handle.
+extern "C" int hp_set_spins(hp_handle* h, const int32_t* q, const int32_t* mp, int32_t is_host, void* stream) {
+    if (!h || !q) return set_error(HP_ERR_ARG, "hp_set_spins: null handle or q");
+    if (!h->q) return set_error(HP_ERR_STATE, "hp_set_spins: no lattice bound");
+    if (mp && !h->mp) return set_error(HP_ERR_STATE, "hp_set_spins: no material-point buffer bound");
+    const size_t bytes = sizeof(int32_t) * (size_t)h->lat.N;
+    const cudaMemcpyKind k = is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = as_stream(stream);
+    HP_CUDA(cudaMemcpyAsync(h->q, q, bytes, k, s));
+    if (mp) HP_CUDA(cudaMemcpyAsync(h->mp, mp, bytes, k, s));
+    return HP_OK;
+}
+
+extern "C" int hp_get_spins(const hp_handle* h, int32_t* q, int32_t* mp, int32_t is_host, void* stream) {
+    if (!h || !q) return set_error(HP_ERR_ARG, "hp_get_spins: null handle or q");
+    if (!h->q) return set_error(HP_ERR_STATE, "hp_get_spins: no lattice bound");
+    if (mp && !h->mp) return set_error(HP_ERR_STATE, "hp_get_spins: no material-point buffer bound");
+    const size_t bytes = sizeof(int32_t) * (size_t)h->lat.N;
+    const cudaMemcpyKind k = is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = as_stream(stream);
+    HP_CUDA(cudaMemcpyAsync(q, h->q, bytes, k, s));
+    if (mp) HP_CUDA(cudaMemcpyAsync(mp, h->mp, bytes, k, s));
     return HP_OK;
 }
 
@@ -200,4 +238,10 @@ extern "C" int hp_philox(uint64_t seed, const uint32_t* ctr, int64_t n, uint32_t
                                                                          reinterpret_cast<uint4*>(out));
     HP_LAUNCH_CHECK("k_philox");
     return HP_OK;
+}
+
+extern "C" int hp_debug_wait_timeout(int32_t unit, int64_t limit_cycles, int32_t late, void* stream) {
+    if (unit == 0) return lean_wait_probe((long long)limit_cycles, late, as_stream(stream));
+    if (unit == 1) return mlp_wait_probe((long long)limit_cycles, late, as_stream(stream));
+    return set_error(HP_ERR_ARG, "hp_debug_wait_timeout: unit must be 0 (sweep) or 1 (surrogate)");
 }

@@ -89,6 +89,10 @@ struct hp_handle {
     uint64_t sweep = 0;
     int sweep_kernel = HP_SWEEP_AUTO;
     int sweep_variant = 0;      // tile variant of the fused kernel (autotuned)
+    // owned scratch of hp_measure (allocated on its first call)
+    unsigned long long* m_counts = nullptr;  // int64[G]
+    int32_t* m_bins = nullptr;               // int32[2G]
+    unsigned long long* m_small = nullptr;   // hist[90] | field sum | alive | bad ids
 };
 
 namespace hp {
@@ -97,4 +101,10 @@ int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s);
 // launchers (voronoi.cu)
 int voronoi_run(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, cudaStream_t s);
 int orientations_run(int32_t G, uint64_t seed, int32_t kind, float* orient, cudaStream_t s);
+// Bounded-wait probes for tests of the timeout paths (lean.cu, mlp.cu): one
+// block waits on an mbarrier with nothing in flight, the arrival coming after
+// two limits (late != 0) or never; the sweep or surrogate timeout flag is
+// raised exactly as by a kernel that timed out.
+int lean_wait_probe(long long limit, int late, cudaStream_t s);
+int mlp_wait_probe(long long limit, int late, cudaStream_t s);
 }  // namespace hp

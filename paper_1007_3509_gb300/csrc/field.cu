@@ -13,6 +13,7 @@
 // counts, number of grains alive, per-grain texture bins and the
 // area-weighted histogram.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -168,6 +169,40 @@ __global__ void k_gaussian_field(int32_t G, const float* angle, double scale, in
     b[g] = (int32_t)rint(256.0 * e);
 }
 
+// Sum over a block of a signed 64-bit value, added to *sum with one atomic
+// (two's complement: the unsigned atomic adds signed values exactly).
+__device__ __forceinline__ void block_add(long long v, unsigned long long* sum) {
+    __shared__ long long part[kT / 32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+#pragma unroll
+        for (int w = 0; w < kT / 32; ++w) t += part[w];
+        if (t) atomicAdd(sum, (unsigned long long)t);
+    }
+}
+
+// Volume-weighted field sum, per-grain table: sum_g counts[g] table[g].
+__global__ void __launch_bounds__(kT) k_field_sum_grain(const unsigned long long* counts, const int32_t* table,
+                                                        int32_t G, unsigned long long* sum) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    block_add(g < G ? (long long)counts[g] * (long long)table[g] : 0ll, sum);
+}
+
+// Per-point table: sum_i table[mp_i] (index clamped into the table).
+__global__ void __launch_bounds__(kT) k_field_sum_point(const int32_t* __restrict__ mp, const int32_t* __restrict__ table,
+                                                        uint32_t n_table, int64_t N, unsigned long long* sum) {
+    long long v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)mp[i];
+        v += table[u < n_table ? u : n_table - 1];
+    }
+    block_add(v, sum);
+}
+
 }  // namespace
 }  // namespace hp
 
@@ -248,5 +283,85 @@ extern "C" int hp_texture(int32_t G, int32_t orient_kind, const float* orient, c
                                                  reinterpret_cast<unsigned long long*>(hist));
     }
     HP_LAUNCH_CHECK("k_bins/k_hist");
+    return HP_OK;
+}
+
+// Slots of the handle's small measurement buffer (unsigned long long each).
+enum { kSlotHist = 0, kSlotField = 90, kSlotAlive = 91, kSlotBad = 92, kSlots = 93 };
+
+extern "C" int hp_measure(hp_handle* h, int32_t orient_kind, const float* orient, int32_t accumulate,
+                          hp_stats* st, int64_t* hist, int32_t n_bins, void* stream) {
+    if (!h || !st) return set_error(HP_ERR_ARG, "hp_measure: null handle or stats");
+    if (!h->q) return set_error(HP_ERR_STATE, "hp_measure: no lattice bound");
+    if (orient && (orient_kind < HP_ORIENT_ANGLE || orient_kind > HP_ORIENT_ZROT))
+        return set_error(HP_ERR_ARG, "hp_measure: bad orient_kind");
+    const int nb = orient ? (orient_kind == HP_ORIENT_SO3 ? 24 : 90) : 0;
+    if (hist && n_bins < nb) return set_error(HP_ERR_ARG, "hp_measure: histogram capacity too small");
+    if (h->desc.field_mode != HP_FIELD_NONE && !h->table)
+        return set_error(HP_ERR_STATE, "hp_measure: no field table set");
+    const int32_t G = h->desc.n_grains;
+    cudaStream_t s = as_stream(stream);
+    if (!h->m_counts) HP_CUDA(cudaMalloc((void**)&h->m_counts, sizeof(unsigned long long) * (size_t)G));
+    if (!h->m_bins) HP_CUDA(cudaMalloc((void**)&h->m_bins, sizeof(int32_t) * 2 * (size_t)G));
+    if (!h->m_small) HP_CUDA(cudaMalloc((void**)&h->m_small, sizeof(unsigned long long) * kSlots));
+    unsigned long long* sm = h->m_small;
+    HP_CUDA(cudaMemsetAsync(h->m_counts, 0, sizeof(unsigned long long) * (size_t)G, s));
+    HP_CUDA(cudaMemsetAsync(sm, 0, sizeof(unsigned long long) * kSlots, s));
+    int32_t* alive = reinterpret_cast<int32_t*>(sm + kSlotAlive);
+    int32_t* bad = reinterpret_cast<int32_t*>(sm + kSlotBad);
+    const int64_t N = h->lat.N;
+    const int64_t threads = (N + kSeg - 1) / kSeg;
+    ::hp::count_launch();
+    k_counts<<<(unsigned)((threads + kT - 1) / kT), kT, 0, s>>>(h->q, N, G, h->m_counts, bad);
+    ::hp::count_launch();
+    k_alive<<<(G + kT - 1) / kT, kT, 0, s>>>(h->m_counts, G, alive);
+    if (orient) {
+        ::hp::count_launch();
+        k_bins<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, orient, h->m_bins);
+        ::hp::count_launch();
+        k_hist<<<(G + kT - 1) / kT, kT, 0, s>>>(G, orient_kind, h->m_bins, h->m_counts, sm + kSlotHist);
+    }
+    if (h->desc.field_mode == HP_FIELD_GRAIN) {
+        ::hp::count_launch();
+        k_field_sum_grain<<<(G + kT - 1) / kT, kT, 0, s>>>(h->m_counts, h->table, G, sm + kSlotField);
+    } else if (h->desc.field_mode == HP_FIELD_POINT) {
+        ::hp::count_launch();
+        k_field_sum_point<<<4 * 152, kT, 0, s>>>(h->mp, h->table, (uint32_t)h->table_n, N, sm + kSlotField);
+    }
+    HP_LAUNCH_CHECK("hp_measure");
+    unsigned long long host[kSlots];
+    HP_CUDA(cudaMemcpyAsync(host, sm, sizeof(host), cudaMemcpyDeviceToHost, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    int32_t nbad = 0, nalive = 0;
+    memcpy(&nbad, &host[kSlotBad], sizeof(int32_t));
+    memcpy(&nalive, &host[kSlotAlive], sizeof(int32_t));
+    if (nbad) return set_error(HP_ERR_STATE, "hp_measure: lattice holds ids outside 0..G-1");
+    if (!accumulate) {
+        memset(st, 0, sizeof(*st));
+        if (hist) memset(hist, 0, sizeof(int64_t) * (size_t)nb);
+    }
+    st->sites += N;
+    st->alive += nalive;
+    st->field_sum += (int64_t)host[kSlotField];
+    if (hist)
+        for (int b = 0; b < nb; ++b) hist[b] += (int64_t)host[kSlotHist + b];
+    // derived figures over everything accumulated so far
+    st->mean_area = st->alive ? (double)st->sites / (double)st->alive : 0.0;
+    st->mean_field = st->sites ? (double)st->field_sum / 256.0 / (double)st->sites : 0.0;
+    if (hist && orient_kind == HP_ORIENT_SO3 && orient) {
+        int64_t tot = 0;
+        double m = 0.0;
+        for (int b = 0; b < 20; ++b) {
+            tot += hist[b];
+            m += (double)hist[b] * (b + 0.5) * (0.5 / 20.0);
+        }
+        st->hist_total = tot;
+        st->mean_mmax = tot ? m / (double)tot : 0.0;
+        for (int f = 0; f < 4; ++f) st->families[f] = tot ? (double)hist[20 + f] / (double)tot : 0.0;
+    } else if (hist && orient) {
+        int64_t tot = 0;
+        for (int b = 0; b < nb; ++b) tot += hist[b];
+        st->hist_total = tot;
+    }
     return HP_OK;
 }

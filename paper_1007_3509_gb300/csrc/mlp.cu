@@ -70,7 +70,7 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar) {
 }
 
 // bounded wait on an mbarrier phase; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t done;
@@ -81,8 +81,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// After a timed-out wait (every thread of the block calls this): wait up to
+// four more limits for the MMA commit that did not arrive (parity phase ^ 1,
+// the phase the block gave up on), so that no tensor-core operation is still
+// writing the accumulators when they are freed.  *err = 1, or 2 if the drain
+// ran out as well (the context must then not be trusted).
+__device__ __forceinline__ void drain_after_timeout(uint32_t mbar, uint32_t phase, int* err) {
+    bool done = false;
+    for (int i = 0; i < 4 && !done; ++i) done = mbar_wait(mbar, phase ^ 1u);
+    const bool all = !__syncthreads_or(!done);
+    if (threadIdx.x == 0) atomicMax(err, all ? 1 : 2);
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
@@ -270,7 +282,7 @@ __global__ void __launch_bounds__(NT) k_mlp_fwd(const float* __restrict__ P, con
         fence_before();
         __syncthreads();
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok) drain_after_timeout(mbar, phase, err);
     fence_before();
     __syncthreads();
     fence_after();
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         if (tid < OUT) atomicAdd(&grads[OB4 + tid], S.gb4[tid]);
         if (tid == 0 && loss) atomicAdd(loss, S.loss * 0.5f * inv_batch);
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok) drain_after_timeout(mbar, phase, err);
     fence_before();
     __syncthreads();
     fence_after();
@@ -641,6 +653,29 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ g, float
 
 int g_err_dev = -1;
 int* g_err = nullptr;
+
+// One block, nothing in flight: an mbarrier that expects one arrival, waited
+// on with a short limit; the arrival comes from thread 32 after two limits
+// (`late`: the drain sees it, flag 1) or never (flag 2).
+__global__ void k_mlp_wait_probe(long long limit, int late, int* err) {
+    __shared__ unsigned long long bar;
+    const uint32_t mb = saddr(&bar);
+    if (threadIdx.x == 0) mbar_init(mb);
+    __syncthreads();
+    if (late && threadIdx.x == 32) {
+        const long long t0 = clock64();
+        while (clock64() - t0 < 2 * limit) {
+        }
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+    }
+    bool ok = mbar_wait(mb, 0u, limit);
+    if (__syncthreads_or(!ok)) {
+        bool done = false;
+        for (int i = 0; i < 4 && !done; ++i) done = mbar_wait(mb, 0u, limit);
+        const bool all = !__syncthreads_or(!done);
+        if (threadIdx.x == 0) atomicMax(err, all ? 1 : 2);
+    }
+}
 
 int error_flag(int** out) {
     int dev = 0;
@@ -725,6 +760,19 @@ extern "C" int hp_mlp_adam(float* params, const float* grads, float* m, float* v
     HP_LAUNCH_CHECK("k_adam");
     return HP_OK;
 }
+
+namespace hp {
+int mlp_wait_probe(long long limit, int late, cudaStream_t s) {
+    if (limit < 1 || limit > kWaitCycles) return set_error(HP_ERR_ARG, "wait probe: limit out of range");
+    int* err = nullptr;
+    int rc = error_flag(&err);
+    if (rc) return rc;
+    count_launch();
+    k_mlp_wait_probe<<<1, 64, 0, s>>>(limit, late, err);
+    HP_LAUNCH_CHECK("k_mlp_wait_probe");
+    return HP_OK;
+}
+}  // namespace hp
 
 extern "C" int hp_mlp_status(int32_t* timed_out) {
     if (!timed_out) return set_error(HP_ERR_ARG, "hp_mlp_status: null argument");

@@ -22,8 +22,6 @@
 // A site whose M neighbours all carry q_i cannot change; it skips the draw.
 #include <string.h>
 
-#include <cudaTypedefs.h>
-
 #include "sweep.cuh"
 
 namespace hp {
@@ -421,317 +419,6 @@ __global__ void __launch_bounds__(kThreads, kPlaneMinBlocks) k_plane_batch(Batch
     plane_body<NBR, WX, TY, FIELD, HASMP>(sa, s_tile, s_zidx, smem);
 }
 
-// ---------------------------------------------------------------------------
-// TMA-fed persistent variant of the fused plane kernel.
-//
-// Same algorithm and result as k_plane; the window is kept row-major so that a
-// tiled TMA copy (cp.async.bulk.tensor) can fill it directly.  Each CTA walks a
-// strided list of (tile, plane) items with two window buffers: while it runs
-// the phases of one item, the TMA copy of its next item is already in flight
-// (completion on an mbarrier; a clock-limited wait raises g_sweep_err and
-// stops the CTA).  Items whose window crosses the periodic boundary are loaded
-// with the wrap-aware vector loads instead (TMA would fill zeros there).
-// Stage A tests pairs of same-colour sites (x, x+2): with the five sites
-// x-1..x+3 of a row held in one aligned 128-bit and one 32-bit shared load.
-// ---------------------------------------------------------------------------
-__device__ int g_sweep_err;
-
-template <int NBR, int WX_, int TY, bool HASMP>
-struct TmaCfg {
-    static constexpr int H = 4, WX = WX_, TX = WX - 2 * H, WY = TY + 2 * H, WN = WX * WY;
-    static constexpr int NP = NBR == 4 ? 2 : 4;
-    static constexpr bool Z = NBR == 26;
-    static constexpr int ARR = 1 + (HASMP ? 1 : 0) + (Z ? 2 : 0);   // q, mp, q(z-1), q(z+1)
-    static constexpr int QCAP = NBR == 4 ? (WX / 2) * WY : (WX / 2) * ((WY + 1) / 2);
-    static constexpr size_t STAGE = sizeof(int32_t) * (size_t)ARR * WN;
-    static constexpr size_t smem() { return 2 * STAGE + sizeof(uint32_t) * QCAP + 64 + 1024; }
-};
-
-
-__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int rank,
-                                         uint32_t mbar) {
-    const uint64_t m = reinterpret_cast<uint64_t>(map);
-    if (rank == 2)
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-            ::"r"(dst), "l"(m), "r"(x), "r"(y), "r"(mbar) : "memory");
-    else
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-            ::"r"(dst), "l"(m), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
-}
-
-// wrap-aware manual load of a row-major window (edge items)
-template <class Cfg>
-__device__ __forceinline__ void load_window_rm(const PlaneArgs& a, const int32_t* __restrict__ src,
-                                               int32_t* __restrict__ dst, int x0, int y0) {
-    constexpr int WX = Cfg::WX, WY = Cfg::WY, H = Cfg::H;
-    if (a.vec) {
-        constexpr int CH = WX / 4;
-        for (int idx = threadIdx.x; idx < CH * WY; idx += kThreads) {
-            const int ly = idx / CH, c = idx - ly * CH;
-            const int gy = wrap1(y0 - H + ly, a.Ly);
-            const int gx = wrap1(x0 - H + 4 * c, a.Lx);
-            *reinterpret_cast<int4*>(dst + ly * WX + 4 * c) =
-                __ldg(reinterpret_cast<const int4*>(src + gx + (int64_t)a.Lx * gy));
-        }
-    } else {
-        for (int idx = threadIdx.x; idx < WX * WY; idx += kThreads) {
-            const int ly = idx / WX, lx = idx - ly * WX;
-            const int gx = a.fast ? wrap1(x0 - H + lx, a.Lx) : wrapi(x0 - H + lx, a.Lx);
-            const int gy = a.fast ? wrap1(y0 - H + ly, a.Ly) : wrapi(y0 - H + ly, a.Ly);
-            dst[idx] = src[gx + (int64_t)a.Lx * gy];
-        }
-    }
-}
-
-template <int NBR, int WX_, int TY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(kThreads, 4)
-    k_plane_tma(PlaneArgs a, const __grid_constant__ CUtensorMap tq, const __grid_constant__ CUtensorMap tmp,
-                const __grid_constant__ CUtensorMap tnb, int total, int rank) {
-    using Cfg = TmaCfg<NBR, WX_, TY, HASMP>;
-    constexpr int H = Cfg::H, WX = Cfg::WX, WY = Cfg::WY, WN = Cfg::WN, TX = Cfg::TX, NP = Cfg::NP;
-    constexpr bool Z = Cfg::Z;
-    constexpr int M = NBR;
-    extern __shared__ __align__(16) unsigned char raw[];
-    unsigned char* base = raw + ((1024 - (s_addr(raw) & 1023)) & 1023);
-    int32_t* bufs = reinterpret_cast<int32_t*>(base);                          // [2][ARR][WN]
-    uint32_t* queue = reinterpret_cast<uint32_t*>(base + 2 * Cfg::STAGE);
-    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(queue + Cfg::QCAP);
-    int* qn = reinterpret_cast<int*>(mbar + 2);
-    const int64_t sxy = (int64_t)a.Lx * a.Ly;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_addr(mbar + i)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    auto item_xyz = [&](int item, int& x0, int& y0, int& z) {
-        const int zidx = item / a.tiles, tile = item - zidx * a.tiles;
-        const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
-        x0 = tx * TX;
-        y0 = ty * TY;
-        z = Z ? 2 * zidx + a.zpar : 0;
-    };
-    auto interior = [&](int x0, int y0) {
-        return a.vec && x0 - H >= 0 && x0 - H + WX <= a.Lx && y0 - H >= 0 && y0 - H + WY <= a.Ly;
-    };
-    // start the copies of an interior item into stage st (one thread)
-    auto issue = [&](int item, int st) {
-        int x0, y0, z;
-        item_xyz(item, x0, y0, z);
-        if (!interior(x0, y0)) return;
-        int32_t* b = bufs + (size_t)st * Cfg::ARR * WN;
-        const uint32_t mb = s_addr(mbar + st);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                     "r"((uint32_t)Cfg::STAGE) : "memory");
-        tma_load(s_addr(b), &tq, x0 - H, y0 - H, z, rank, mb);
-        int k = 1;
-        if (HASMP) tma_load(s_addr(b + (k++) * WN), &tmp, x0 - H, y0 - H, z, rank, mb);
-        if (Z) {
-            tma_load(s_addr(b + (k++) * WN), &tnb, x0 - H, y0 - H, (z + a.Lz - 1) % a.Lz, rank, mb);
-            tma_load(s_addr(b + k * WN), &tnb, x0 - H, y0 - H, (z + 1) % a.Lz, rank, mb);
-        }
-    };
-
-    constexpr int PAIRS = WX / 4;
-    const int lane_p = threadIdx.x % PAIRS;
-    const int row_slot = threadIdx.x / PAIRS;
-    constexpr int ROWS_PER_PASS = kThreads / PAIRS;
-    const int cz = Z ? 4 * a.zpar : 0;
-    uint32_t phase0 = 0u, phase1 = 0u;  // mbarrier phase of each stage
-    bool ok = true;
-
-    int st = 0;
-    if (threadIdx.x == 0 && (int)blockIdx.x < total) issue(blockIdx.x, 0);
-    for (int item = blockIdx.x; item < total; item += gridDim.x, st ^= 1) {
-        const int next = item + gridDim.x;
-        if (threadIdx.x == 0 && next < total) issue(next, st ^ 1);
-        int x0, y0, z;
-        item_xyz(item, x0, y0, z);
-        int32_t* b = bufs + (size_t)st * Cfg::ARR * WN;
-        int32_t* s_q = b;
-        int32_t* s_mp = HASMP ? b + WN : nullptr;
-        int32_t* s_lo = Z ? b + (HASMP ? 2 : 1) * WN : nullptr;
-        int32_t* s_hi = Z ? s_lo + WN : nullptr;
-        const int zlo = Z ? (z + a.Lz - 1) % a.Lz : 0, zhi = Z ? (z + 1) % a.Lz : 0;
-        if (threadIdx.x < 8) qn[threadIdx.x] = 0;
-        if (interior(x0, y0)) {
-            const bool w = wait_parity(s_addr(mbar + st), st ? phase1 : phase0);
-            if (st) phase1 ^= 1u; else phase0 ^= 1u;
-            if (__syncthreads_or(!w)) { ok = false; break; }
-        } else {
-            load_window_rm<Cfg>(a, a.q_in + sxy * z, s_q, x0, y0);
-            if (HASMP) load_window_rm<Cfg>(a, a.mp_in + sxy * z, s_mp, x0, y0);
-            if (Z) {
-                load_window_rm<Cfg>(a, a.q_nb + sxy * zlo, s_lo, x0, y0);
-                load_window_rm<Cfg>(a, a.q_nb + sxy * zhi, s_hi, x0, y0);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            const int lo = p + 1, hix = WX - p - 1, hiy = WY - p - 1;
-            constexpr int RSTEP = NBR == 4 ? 1 : 2;
-            const int ys = NBR == 4 ? lo : lo + ((lo ^ (p >> 1)) & 1);
-            for (int ly0 = ys; ly0 < hiy; ly0 += RSTEP * ROWS_PER_PASS) {
-                const int ly = ly0 + RSTEP * row_slot;
-                const int px = NBR == 4 ? ((ly + p) & 1) : (p & 1);
-                const bool rowok = ly < hiy;
-                const int lxa = 4 * lane_p + px, lxb = lxa + 2;
-                const bool va = rowok && lxa >= lo && lxa < hix;
-                const bool vb = rowok && lxb >= lo && lxb < hix;
-                int same_a = 0, same_b = 0;
-                if (va || vb) {
-                    const int rq = ly * WX + 4 * lane_p;                       // aligned quad of the row
-                    const int r1 = ly * WX + (px ? min(4 * lane_p + 4, WX - 1) : max(4 * lane_p - 1, 0));
-                    // e(k) = element at lxa + k, k = -1..3
-                    auto row = [&](const int32_t* P, int o, int& ea_m1, int& e0, int& e1, int& e2, int& e3) {
-                        const int4 qd = *reinterpret_cast<const int4*>(P + rq + o);
-                        const int32_t sg = P[r1 + o];
-                        if (px) { ea_m1 = qd.x; e0 = qd.y; e1 = qd.z; e2 = qd.w; e3 = sg; }
-                        else { ea_m1 = sg; e0 = qd.x; e1 = qd.y; e2 = qd.z; e3 = qd.w; }
-                    };
-                    int m1, e0, e1, e2, e3;
-                    row(s_q, 0, m1, e0, e1, e2, e3);
-                    const int32_t qa = e0, qb = e2;
-                    same_a = (m1 == qa) + (e1 == qa);
-                    same_b = (e1 == qb) + (e3 == qb);
-                    if (NBR == 4) {
-                        row(s_q, -WX, m1, e0, e1, e2, e3);
-                        same_a += e0 == qa; same_b += e2 == qb;
-                        row(s_q, WX, m1, e0, e1, e2, e3);
-                        same_a += e0 == qa; same_b += e2 == qb;
-                    } else {
-                        auto full = [&](const int32_t* P, int o) {
-                            int n1, f0, f1, f2, f3;
-                            row(P, o, n1, f0, f1, f2, f3);
-                            same_a += (n1 == qa) + (f0 == qa) + (f1 == qa);
-                            same_b += (f1 == qb) + (f2 == qb) + (f3 == qb);
-                        };
-                        full(s_q, -WX);
-                        full(s_q, WX);
-                        if (Z) {
-#pragma unroll
-                            for (int dy = -1; dy <= 1; ++dy) {
-                                full(s_lo, dy * WX);
-                                full(s_hi, dy * WX);
-                            }
-                        }
-                    }
-                }
-                const int lane = threadIdx.x & 31;
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const bool cand = hh == 0 ? (va && same_a != M) : (vb && same_b != M);
-                    const unsigned ball = __ballot_sync(0xFFFFFFFFu, cand);
-                    if (ball) {
-                        int slot = 0;
-                        if (lane == __ffs(ball) - 1) slot = atomicAdd(qn + p, __popc(ball));
-                        slot = __shfl_sync(0xFFFFFFFFu, slot, __ffs(ball) - 1);
-                        if (cand) {
-                            const int kq = slot + __popc(ball & ((1u << lane) - 1));
-                            const int lx = hh == 0 ? lxa : lxb, same = hh == 0 ? same_a : same_b;
-                            queue[kq] = ((uint32_t)ly << 13) | ((uint32_t)lx << 5) | (uint32_t)same;
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            const int n = qn[p];
-            for (int k = threadIdx.x; k < n; k += kThreads) {
-                const uint32_t e = queue[k];
-                const int same_old = (int)(e & 31u), lx = (int)((e >> 5) & 255u), ly = (int)(e >> 13);
-                const int li = ly * WX + lx;
-                const int32_t qi = s_q[li];
-                const int gx = a.fast ? wrap1(x0 - H + lx, a.Lx) : wrapi(x0 - H + lx, a.Lx);
-                const int gy = a.fast ? wrap1(y0 - H + ly, a.Ly) : wrapi(y0 - H + ly, a.Ly);
-                const int64_t gi = gx + (int64_t)a.Lx * gy + sxy * z;
-                const int colour = NBR == 4 ? p : cz + p;
-                const uint4 u = draw(a.seed, (uint64_t)gi, a.sweep, kTagSweep, (uint32_t)colour);
-                const int kp = (int)__umulhi(u.x, (uint32_t)M);
-                int dx, dy, dz;
-                if (NBR == 4) Geo<2, 4>::off(kp, dx, dy, dz);
-                else if (NBR == 8) Geo<2, 8>::off(kp, dx, dy, dz);
-                else Geo<3, 26>::off(kp, dx, dy, dz);
-                const int lj = li + dy * WX + dx;
-                const int32_t* pj = dz == 0 ? s_q : (dz < 0 ? s_lo : s_hi);
-                const int32_t qj = pj[lj];
-                if (qj == qi) continue;
-                int32_t mpj = 0;
-                if (HASMP) {
-                    if (dz == 0) {
-                        mpj = s_mp[lj];
-                    } else {
-                        const int jx = wrap1(gx + dx, a.Lx), jy = wrap1(gy + dy, a.Ly);
-                        mpj = __ldg(a.mp_nb + jx + (int64_t)a.Lx * jy + sxy * (dz < 0 ? zlo : zhi));
-                    }
-                }
-                int32_t bi = 0, bj = 0;
-                if (FIELD == 1) { bi = tab(a.table, a.table_n, qi); bj = tab(a.table, a.table_n, qj); }
-                if (FIELD == 2) { bi = tab(a.table, a.table_n, s_mp[li]); bj = tab(a.table, a.table_n, mpj); }
-                int same_new = 0;
-                if (NBR == 4) {
-                    same_new = (s_q[li - 1] == qj) + (s_q[li + 1] == qj) + (s_q[li - WX] == qj) + (s_q[li + WX] == qj);
-                } else {
-#pragma unroll
-                    for (int ddy = -1; ddy <= 1; ++ddy)
-#pragma unroll
-                        for (int ddx = -1; ddx <= 1; ++ddx) {
-                            const int o = li + ddy * WX + ddx;
-                            if (ddx || ddy) same_new += s_q[o] == qj;
-                            if (Z) same_new += (s_lo[o] == qj) + (s_hi[o] == qj);
-                        }
-                }
-                const int32_t d = a.J * (same_old - same_new) + (bj - bi);
-                if (metropolis(d, a.D, a.thr, u.y)) {
-                    s_q[li] = qj;
-                    if (HASMP) s_mp[li] = mpj;
-                }
-            }
-            __syncthreads();
-        }
-        // write the core
-        int32_t* qo = a.q_out + sxy * z;
-        int32_t* mpo = HASMP ? a.mp_out + sxy * z : nullptr;
-        if (a.vec) {
-            constexpr int CH = TX / 4;
-            for (int idx = threadIdx.x; idx < CH * TY; idx += kThreads) {
-                const int cy = idx / CH, c = idx - cy * CH;
-                const int gx = x0 + 4 * c, gy = y0 + cy;
-                if (gx >= a.Lx || gy >= a.Ly) continue;
-                const int r = (cy + H) * WX + H + 4 * c;
-                *reinterpret_cast<int4*>(qo + gx + (int64_t)a.Lx * gy) = *reinterpret_cast<const int4*>(s_q + r);
-                if (HASMP)
-                    *reinterpret_cast<int4*>(mpo + gx + (int64_t)a.Lx * gy) = *reinterpret_cast<const int4*>(s_mp + r);
-            }
-        } else {
-            for (int idx = threadIdx.x; idx < TX * TY; idx += kThreads) {
-                const int cy = idx / TX, cx = idx - cy * TX;
-                const int gx = x0 + cx, gy = y0 + cy;
-                if (gx >= a.Lx || gy >= a.Ly) continue;
-                const int r = (cy + H) * WX + cx + H;
-                qo[gx + (int64_t)a.Lx * gy] = s_q[r];
-                if (HASMP) mpo[gx + (int64_t)a.Lx * gy] = s_mp[r];
-            }
-        }
-        // the buffer is refilled by TMA two items later: order our writes before it
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-    }
-    if (!ok) {
-        if (threadIdx.x == 0) {
-            atomicExch(&g_sweep_err, 1);
-            // let a copy still in flight into the other buffer finish (bounded)
-            wait_parity(s_addr(mbar + (st ^ 1)), st ? phase0 : phase1);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Host dispatch
-// ---------------------------------------------------------------------------
 template <int DIM, int NBR, int FIELD, bool HASMP>
 int launch_phase(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     PhaseArgs a;
@@ -777,37 +464,31 @@ int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     return phase_dispatch<3, 26>(h, sweep, colour, s);
 }
 
-// Tile variants of the fused kernel: window width WX (core TX = WX - 8) and
-// core height TY, plain (parity-split window, one CTA per item) or TMA-fed
-// (row-major window, persistent CTAs).  All give identical lattices; the
-// autotuner picks one.  TMA variants serve single lattices only.
-// Strip variants (strip.cu): one warp per strip, WX = 32 x columns per lane,
-// TY = most core rows per strip.  Tile variants (tile.cu): WX x (TY + 4)
-// windows fed by bulk TMA copies.
+// Tile variants of the fused kernel.  Plane tiles (this file): window width WX
+// (core TX = WX - 8) and core height TY, parity-split window, one CTA per item.
+// Lean tiles (tile.cu): WX x (TY + 4) row-major windows fed by bulk TMA copies.
+// Lean 3D windows (lean.cu, 26 neighbours): 64 x (TY + 4), every draw made
+// while the window is in flight.  All give identical lattices; the autotuner
+// picks one.  Ensembles take the plane and lean tiles.
 struct Variant {
     int WX, TY;
-    bool tma;
-    bool strip;
     bool tile;
+    bool lean;
 };
-constexpr int kVariants2D = 12, kVariants3D = 13;
+constexpr int kVariants2D = 6, kVariants3D = 12;
 constexpr Variant kV2D[kVariants2D] = {
-    {128, 64, false, false, false}, {128, 32, false, false, false}, {64, 64, false, false, false},
-    {128, 32, true, false, false},  {128, 24, true, false, false},  {256, 16, false, true, false},
-    {256, 32, false, true, false},  {128, 16, false, true, false},  {128, 32, false, true, false},
-    {128, 28, false, false, true},  {128, 60, false, false, true},  {64, 60, false, false, true}};
+    {128, 64, false, false}, {128, 32, false, false}, {64, 64, false, false},
+    {128, 28, true, false},  {128, 60, true, false},  {64, 60, true, false}};
 constexpr Variant kV3D[kVariants3D] = {
-    {128, 32, false, false, false}, {128, 16, false, false, false}, {64, 32, false, false, false},
-    {64, 16, false, false, false},  {64, 32, true, false, false},   {64, 16, true, false, false},
-    {64, 64, false, true, false},   {128, 64, false, true, false},  {64, 32, false, true, false},
-    {64, 60, false, false, true},   {64, 28, false, false, true},   {128, 28, false, false, true},
-    {64, 36, false, false, true}};
+    {128, 32, false, false}, {128, 16, false, false}, {64, 32, false, false}, {64, 16, false, false},
+    {64, 60, true, false},   {64, 28, true, false},   {128, 28, true, false}, {64, 36, true, false},
+    {64, 40, false, true},   {64, 36, false, true},   {64, 32, false, true}, {64, 28, false, true}};
 
 int n_variants(int nbr) { return nbr == 26 ? kVariants3D : (nbr == 6 ? 1 : kVariants2D); }
 Variant variant_of(int nbr, int v) { return nbr == 26 ? kV3D[v] : kV2D[v]; }
 // Window rows: tile windows carry two halo rows above and below the core, the
 // plane kernels four.
-int window_rows(const Variant& v) { return v.TY + (v.tile ? 4 : 8); }
+int window_rows(const Variant& v) { return v.TY + (v.tile || v.lean ? 4 : 8); }
 
 template <int NBR, int WX, int TY, int FIELD, bool HASMP>
 int launch_one(const PlaneArgs* a, const BatchArgs* b, int64_t blocks, int planes, cudaStream_t s) {
@@ -829,66 +510,6 @@ int launch_one(const PlaneArgs* a, const BatchArgs* b, int64_t blocks, int plane
     return HP_OK;
 }
 
-// ---- TMA tensor maps --------------------------------------------------------
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// Map of an int32 lattice (rank 2 in 2D, 3 in 3D) with a WX x WY (x 1) box.
-int make_map(CUtensorMap* m, const void* base, const PlaneArgs& a, int rank, int WX, int WY) {
-    memset(m, 0, sizeof(*m));
-    if (!a.vec || !base) return HP_OK;  // never dereferenced: every item takes the manual path
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) return set_error(HP_ERR_CUDA, "sweep: cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[3] = {(cuuint64_t)a.Lx, (cuuint64_t)a.Ly, (cuuint64_t)a.Lz};
-    cuuint64_t strides[2] = {(cuuint64_t)a.Lx * 4, (cuuint64_t)a.Lx * a.Ly * 4};
-    cuuint32_t box[3] = {(cuuint32_t)WX, (cuuint32_t)WY, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_INT32, (cuuint32_t)rank, const_cast<void*>(base), dims, strides,
-                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return set_error(HP_ERR_CUDA, "sweep: cuTensorMapEncodeTiled failed");
-    return HP_OK;
-}
-
-template <int NBR, int WX, int TY, int FIELD, bool HASMP>
-int launch_tma(const PlaneArgs& a, int planes, cudaStream_t s) {
-    using Cfg = TmaCfg<NBR, WX, TY, HASMP>;
-    auto fn = k_plane_tma<NBR, WX, TY, FIELD, HASMP>;
-    const size_t smem = Cfg::smem();
-    static int per_sm = 0;
-    if (!per_sm) {
-        HP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        HP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
-        if (per_sm < 1) return set_error(HP_ERR_CUDA, "sweep: TMA variant does not fit on an SM");
-    }
-    const int rank = NBR == 26 ? 3 : 2;
-    CUtensorMap tq, tmp, tnb;
-    int rc = make_map(&tq, a.q_in, a, rank, WX, Cfg::WY);
-    if (!rc) rc = make_map(&tmp, HASMP ? a.mp_in : nullptr, a, rank, WX, Cfg::WY);
-    if (!rc) rc = make_map(&tnb, NBR == 26 ? a.q_nb : nullptr, a, rank, WX, Cfg::WY);
-    if (rc) return rc;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t total = (int64_t)a.tiles * planes;
-    const int64_t grid = total < (int64_t)sms * per_sm ? total : (int64_t)sms * per_sm;
-    ::hp::count_launch();
-    fn<<<(unsigned)grid, kThreads, smem, s>>>(a, tq, tmp, tnb, (int)total, rank);
-    HP_LAUNCH_CHECK("k_plane_tma");
-    return HP_OK;
-}
-
 // field / material-point combinations; variants other than 0 are compiled for
 // the two production combinations only (grain field without mp, point field)
 template <int NBR, int WX, int TY, bool ALL>
@@ -904,63 +525,49 @@ int launch_fm(int field, bool m, const PlaneArgs* a, const BatchArgs* b, int64_t
     return set_error(HP_ERR_ARG, "sweep: tile variant not built for this field mode");
 }
 
-template <int NBR, int WX, int TY>
-int launch_fm_tma(int field, bool m, const PlaneArgs* a, int planes, cudaStream_t s) {
-    if (!a) return set_error(HP_ERR_ARG, "sweep: TMA variants serve single lattices only");
-    if (field == HP_FIELD_GRAIN && !m) return launch_tma<NBR, WX, TY, 1, false>(*a, planes, s);
-    if (field == HP_FIELD_POINT) return launch_tma<NBR, WX, TY, 2, true>(*a, planes, s);
-    return set_error(HP_ERR_ARG, "sweep: tile variant not built for this field mode");
-}
-
 int launch_variant(int nbr, int v, int field, bool m, const PlaneArgs* a, const BatchArgs* b, int64_t blocks,
                    int planes, cudaStream_t s) {
     const Variant var = variant_of(nbr, v);
+    if (var.lean) {
+        if (!a) return set_error(HP_ERR_ARG, "sweep: lean variants serve single lattices only");
+        return blocks == 0 ? HP_OK : lean_launch(*a, field, m, planes, window_rows(var), s);
+    }
     if (var.tile) {
         if (a) return blocks == 0 ? HP_OK : tile_launch(*a, field, m, nbr, planes, var.WX, window_rows(var), s);
         return tile_launch_batch(b->args, b->start, b->R, blocks, b->sweep_add, field, m, nbr, var.WX,
                                  window_rows(var), s);
     }
-    if (var.strip) {
-        if (!a) return set_error(HP_ERR_ARG, "sweep: strip variants serve single lattices only");
-        if (blocks == 0) return HP_OK;
-        return strip_launch(*a, field, m, nbr, planes, var.WX / 32, var.TY, s);
-    }
     if (nbr == 4) {
         switch (v) {
             case 0: return launch_fm<4, 128, 64, true>(field, m, a, b, blocks, planes, s);
             case 1: return launch_fm<4, 128, 32, false>(field, m, a, b, blocks, planes, s);
-            case 2: return launch_fm<4, 64, 64, false>(field, m, a, b, blocks, planes, s);
-            case 3: return launch_fm_tma<4, 128, 32>(field, m, a, planes, s);
-            default: return launch_fm_tma<4, 128, 24>(field, m, a, planes, s);
+            default: return launch_fm<4, 64, 64, false>(field, m, a, b, blocks, planes, s);
         }
     }
     if (nbr == 8) {
         switch (v) {
             case 0: return launch_fm<8, 128, 64, true>(field, m, a, b, blocks, planes, s);
             case 1: return launch_fm<8, 128, 32, false>(field, m, a, b, blocks, planes, s);
-            case 2: return launch_fm<8, 64, 64, false>(field, m, a, b, blocks, planes, s);
-            case 3: return launch_fm_tma<8, 128, 32>(field, m, a, planes, s);
-            default: return launch_fm_tma<8, 128, 24>(field, m, a, planes, s);
+            default: return launch_fm<8, 64, 64, false>(field, m, a, b, blocks, planes, s);
         }
     }
     switch (v) {
         case 0: return launch_fm<26, 128, 32, true>(field, m, a, b, blocks, planes, s);
         case 1: return launch_fm<26, 128, 16, false>(field, m, a, b, blocks, planes, s);
         case 2: return launch_fm<26, 64, 32, false>(field, m, a, b, blocks, planes, s);
-        case 3: return launch_fm<26, 64, 16, false>(field, m, a, b, blocks, planes, s);
-        case 4: return launch_fm_tma<26, 64, 32>(field, m, a, planes, s);
-        default: return launch_fm_tma<26, 64, 16>(field, m, a, planes, s);
+        default: return launch_fm<26, 64, 16, false>(field, m, a, b, blocks, planes, s);
     }
 }
 
 bool variant_ok(int nbr, int v, int field, bool m) {
     if (v < 0 || v >= n_variants(nbr)) return false;
+    if (variant_of(nbr, v).lean) return true;  // built for every field mode
     return v == 0 || (field == HP_FIELD_GRAIN && !m) || field == HP_FIELD_POINT;
 }
 
 bool variant_batch_ok(int nbr, int v, int field, bool m) {
     const Variant var = variant_of(nbr, v);
-    return variant_ok(nbr, v, field, m) && !var.tma && !var.strip;
+    return variant_ok(nbr, v, field, m) && !var.lean;
 }
 
 // Arguments of the fused kernel for one lattice and one launch.
@@ -1242,14 +849,11 @@ extern "C" int hp_set_sweep_variant(hp_handle* h, int32_t v) {
 
 extern "C" int hp_sweep_status(int32_t* timed_out) {
     if (!timed_out) return set_error(HP_ERR_ARG, "hp_sweep_status: null argument");
-    int v = 0, vs = 0, zero = 0;
-    HP_CUDA(cudaMemcpyFromSymbol(&v, g_sweep_err, sizeof(int)));
-    if (v) HP_CUDA(cudaMemcpyToSymbol(g_sweep_err, &zero, sizeof(int)));
-    int vt = 0;
-    int rc = strip_status(&vs);
-    if (!rc) rc = tile_status(&vt);
+    int vt = 0, vl = 0;
+    int rc = tile_status(&vt);
+    if (!rc) rc = lean_status(&vl);
     if (rc) return rc;
-    *timed_out = (v || vs || vt) ? 1 : 0;
+    *timed_out = vt > vl ? vt : vl;
     if (*timed_out) return set_error(HP_ERR_TIMEOUT, "sweep: a TMA copy did not complete in time");
     return HP_OK;
 }

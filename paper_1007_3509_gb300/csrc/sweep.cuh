@@ -1,4 +1,4 @@
-// Device helpers shared by the sweep kernels (sweep.cu, strip.cu): lattice
+// Device helpers shared by the sweep kernels (sweep.cu, tile.cu, lean.cu): lattice
 // neighbourhoods and colourings (Sec. 4), the integer Metropolis test (Eq. (7)
 // with the acceptance table of Sec. 4), periodic wrapping, the launch
 // arguments of one fused sweep launch, and the mbarrier wait used by the
@@ -106,19 +106,45 @@ __device__ __forceinline__ int32_t tab(const int32_t* __restrict__ t, uint32_t n
 
 __device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Wait for an mbarrier phase with a clock limit (about two seconds); false on
-// timeout.
-__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+// Wait for an mbarrier phase with a clock limit (default about two seconds at
+// the boost clock); false on timeout.  Each try_wait may suspend the thread for
+// up to 20 us (it wakes as soon as the phase completes), so a waiting warp
+// issues few instructions.
+constexpr long long kWaitCycles = 1ll << 32;
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     for (;;) {
         uint32_t done;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+            : "=r"(done) : "r"(mbar), "r"(parity), "r"(20000u) : "memory");
         if (done) return true;
-        if (clock64() - t0 > (1ll << 32)) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+// Block-wide wait for a window's bulk copies (every thread calls it).  Warp 0
+// polls the barrier while the other warps wait at the block barrier (issuing
+// nothing); once the copies have landed every thread observes the completed
+// phase itself (a try_wait that succeeds at once), which orders its reads
+// after the copies.  On a timeout every thread of the block keeps waiting, up
+// to four more limits, so that no copy is still landing in this block's shared
+// memory when it leaves; *flag becomes 1, or 2 if even that drain ran out
+// (copies may still have been in flight at exit: the context must not be
+// trusted).  False after a timeout.
+__device__ __forceinline__ bool wait_or_drain(uint32_t mbar, int* flag, long long limit = kWaitCycles) {
+    bool ok = true;
+    if (threadIdx.x < 32) ok = wait_parity(mbar, 0u, limit);
+    if (!__syncthreads_or(!ok)) {
+        if (threadIdx.x >= 32) wait_parity(mbar, 0u, limit);
+        return true;
+    }
+    bool drained = false;
+    for (int i = 0; i < 5 && !drained; ++i) drained = wait_parity(mbar, 0u, limit);
+    const bool all = !__syncthreads_or(!drained);
+    if (threadIdx.x == 0) atomicMax(flag, all ? 1 : 2);
+    return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const int32_t* src, uint32_t bytes, uint32_t mbar) {
@@ -152,11 +178,11 @@ int tile_launch_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, in
 // Reads and clears the tile kernel's timeout flag.
 int tile_status(int* timed_out);
 
-// Strip kernel (strip.cu): one launch over the planes of one parity.
-// cpl = columns per lane (2 or 4), ty_max = most core rows per strip.
-int strip_launch(const PlaneArgs& a, int field, bool hasmp, int nbr, int planes, int cpl, int ty_max,
-                 cudaStream_t s);
-// Reads and clears the strip kernel's timeout flag.
-int strip_status(int* timed_out);
+// Lean 3D kernel (lean.cu): one launch over the planes of one parity; 64 x WY
+// windows (WY 40 or 44), draws made while the window is in flight.
+int lean_launch(const PlaneArgs& a, int field, bool hasmp, int planes, int WY, cudaStream_t s);
+// Reads and clears the lean kernel's timeout flag (2: a drain ran out too).
+int lean_status(int* timed_out);
+
 
 }  // namespace hp

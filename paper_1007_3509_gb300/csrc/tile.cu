@@ -187,7 +187,6 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
         return a.q_nb + sxy * (arr == Cfg::A_LO ? t.zlo : t.zhi);
     };
     if (threadIdx.x < 4) qn[threadIdx.x] = 0;
-    bool ok = true;
     if (tma) {
         const uint32_t mb = s_addr(mbar);
         if (threadIdx.x == 0) {
@@ -205,14 +204,7 @@ __device__ __forceinline__ void tile_body(const PlaneArgs& a, const int tile, co
                 copy_row(base + arr * AS + PAD + r * WX, src(arr) + (int64_t)a.Lx * t.gy_of(r), t.x0 - 4, WX, a.Lx, mb);
             }
         }
-        ok = wait_parity(mb, 0u);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                atomicExch(&g_tile_err, 1);
-                wait_parity(mb, 0u);  // the copies in flight land before the block leaves (bounded)
-            }
-            return;
-        }
+        if (!wait_or_drain(mb, &g_tile_err)) return;
     } else {
         for (int i = threadIdx.x; i < ARR * WY * WX; i += kTileThreads) {
             const int arr = i / (WY * WX), rem = i - arr * (WY * WX), r = rem / WX, c = rem - r * WX;

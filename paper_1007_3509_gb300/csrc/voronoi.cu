@@ -15,7 +15,6 @@
 // outside the scanned rings can have (wmin = narrowest cell width).
 #include <math.h>
 
-#include <mutex>
 
 #include "common.cuh"
 
@@ -288,28 +287,29 @@ int voronoi_run(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_
 namespace hp {
 namespace {
 
-constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB
+constexpr size_t kStaticScratchBytes = (size_t)HP_VORONOI_STATIC_BYTES;
 static __device__ __align__(256) unsigned char g_vor_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+// Worst case of the carve below at HP_VORONOI_STATIC_MAX_GRAINS on a square or
+// cubic lattice: int64 seed sites (8 G), int4 seed coordinates and the int4
+// cell list (16 G each), and three int32 cell arrays of at most G/2 + 1 cells
+// (the cell edge is (2N/G)^(1/dim)), each carve rounded up to 256 bytes.
+// Thin lattices whose cell count rounds up past G/2 are caught at run time.
+static_assert((size_t)HP_VORONOI_STATIC_MAX_GRAINS * (8 + 16 + 16) +
+                      3 * ((size_t)HP_VORONOI_STATIC_MAX_GRAINS / 2 + 2) * 4 + 7 * 256 <=
+                  kStaticScratchBytes,
+              "static Voronoi scratch too small for HP_VORONOI_STATIC_MAX_GRAINS");
 
 // Device address of the static scratch on the current device.  The array's
 // name is only a host-side stand-in; its device address comes from
-// cudaGetSymbolAddress, taken once per device with that device current.
+// cudaGetSymbolAddress, taken on every call with the caller's device current
+// (nothing is cached, so a context torn down and created again between calls
+// never leaves a stale address behind).
 int static_scratch(void** out) {
-    int dev = 0;
-    HP_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return set_error(HP_ERR_ARG, "hp_init_voronoi_static: device ordinal too large");
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_vor_scratch);
-        if (e != cudaSuccess) return cuda_error(e, "hp_init_voronoi_static: cudaGetSymbolAddress");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_vor_scratch);
+    if (e != cudaSuccess) return cuda_error(e, "hp_init_voronoi_static: cudaGetSymbolAddress");
+    *out = p;
     return HP_OK;
 }
 

@@ -48,6 +48,23 @@ class hp_sur_scales(C.Structure):
     _fields_ = [("stress", C.c_float), ("strain", C.c_float), ("w", C.c_float), ("erho", C.c_float)]
 
 
+class hp_stats(C.Structure):
+    _fields_ = [("sites", C.c_int64), ("alive", C.c_int64), ("mean_area", C.c_double), ("field_sum", C.c_int64),
+                ("mean_field", C.c_double), ("hist_total", C.c_int64), ("families", C.c_double * 4),
+                ("mean_mmax", C.c_double)]
+
+    def as_dict(self):
+        return {"sites": self.sites, "alive": self.alive, "mean_area": self.mean_area, "field_sum": self.field_sum,
+                "mean_field": self.mean_field, "hist_total": self.hist_total, "families": list(self.families),
+                "mean_mmax": self.mean_mmax}
+
+
+class hp_sur_train_params(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("batch", C.c_int64), ("group", C.c_int32), ("lr", C.c_float),
+                ("lr_floor", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("log_every", C.c_int32)]
+
+
 class hp_cp_state(C.Structure):
     _fields_ = [("P", C.c_int64), ("eps_p", C.c_void_p), ("gamma", C.c_void_p), ("g", C.c_void_p)]
 
@@ -55,6 +72,13 @@ class hp_cp_state(C.Structure):
 _SIGS = {
     "hp_last_error_message": ([], C.c_char_p),
     "hp_version": ([], C.c_char_p),
+    "hp_last_error": ([C.c_void_p, C.c_char_p, C.c_size_t], C.c_int),
+    "hp_set_spins": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "hp_get_spins": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "hp_measure": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(hp_stats), C.c_void_p, C.c_int32,
+                    C.c_void_p], C.c_int),
+    "hp_sur_train": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                      C.POINTER(hp_sur_train_params), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_kernel_launches": ([C.POINTER(C.c_uint64)], C.c_int),
     "hp_create": ([C.POINTER(hp_desc), C.POINTER(C.c_void_p)], C.c_int),
     "hp_destroy": ([C.c_void_p], C.c_int),
@@ -69,6 +93,7 @@ _SIGS = {
     "hp_sweep": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "hp_sweep_variants": ([C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "hp_sweep_status": ([C.POINTER(C.c_int32)], C.c_int),
+    "hp_debug_wait_timeout": ([C.c_int32, C.c_int64, C.c_int32, C.c_void_p], C.c_int),
     "hp_set_sweep_variant": ([C.c_void_p, C.c_int32], C.c_int),
     "hp_sweep_autotune": ([C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p], C.c_int),
     "hp_ensemble_create": ([C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
@@ -165,6 +190,24 @@ def _stream(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def _host(a, n, dtype, what):
+    """Host pointer of a numpy array or CPU torch tensor of at least n elements
+    of `dtype` (contiguous); the array itself is returned too, to be kept alive."""
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda:
+            raise HPError(HP_ERR_ARG, f"{what}: expected a host buffer")
+        a = a.numpy()
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"] or a.size < n:
+        raise HPError(HP_ERR_ARG, f"{what}: needs a contiguous {np.dtype(dtype).name} host array of >= {n} elements")
+    return a.ctypes.data, a
+
+
+def hp_last_error(n=512) -> str:
+    buf = C.create_string_buffer(n)
+    _check(lib().hp_last_error(None, buf, n))
+    return buf.value.decode()
 
 
 def version() -> str:
@@ -287,6 +330,21 @@ def hp_sur_field(params, quat, G, load, energy_scale, b_out, e_out=None, scales=
                               _stream(stream)))
 
 
+def hp_sur_train(params, m, v, X, Y, steps, batch=65536, group=1, lr=2e-3, lr_floor=0.02, beta1=0.9, beta2=0.999,
+                 eps=1e-8, step0=0, loss=None, log_every=0, stream=None):
+    """Adam training loop of the library (minibatches of whole row groups, cosine
+    learning-rate decay); returns the host loss log (numpy float32, may be empty)."""
+    M, P, w = int(X.shape[0]), hp_mlp_param_count(), "hp_sur_train"
+    tp = hp_sur_train_params(int(steps), int(batch or 0), int(group), float(lr), float(lr_floor), float(beta1),
+                             float(beta2), float(eps), int(log_every))
+    log = np.zeros(max(1, int(steps) // int(log_every)) if log_every else 1, dtype=np.float32)
+    _check(lib().hp_sur_train(_dev(params, P, 4, w + " params"), _dev(m, P, 4, w + " m"), _dev(v, P, 4, w + " v"),
+                              _dev(X, 11 * M, 4, w + " X"), _dev(Y, 2 * M, 4, w + " Y"), M, C.byref(tp), int(step0),
+                              _dev(loss, 1, 4, w + " loss"), log.ctypes.data if log_every else None,
+                              _stream(stream)))
+    return log[: int(steps) // int(log_every)] if log_every else log[:0]
+
+
 def cp_params(C11, C12, C44, tau0, taus, h0, beta, e_incr, energy_scale=1.0, G=None, w_weight=1.0):
     if G is None:
         G = (C11 - C12 + 3.0 * C44) / 5.0
@@ -315,6 +373,11 @@ def hp_sweep_status():
     v = C.c_int32(0)
     _check(lib().hp_sweep_status(C.byref(v)))
     return v.value
+
+
+def hp_debug_wait_timeout(unit, limit_cycles, late=True, stream=None):
+    """Run the bounded-wait probe of the sweep (unit 0) or surrogate (unit 1) kernels."""
+    _check(lib().hp_debug_wait_timeout(int(unit), int(limit_cycles), 1 if late else 0, _stream(stream)))
 
 
 def hp_sweep_variants(nbr):
@@ -439,6 +502,40 @@ class Lattice:
 
     def hp_checkpoint_load(self, path, stream=None):
         _check(lib().hp_checkpoint_load(self._h, str(path).encode(), _stream(stream)))
+
+    def hp_set_spins(self, q, mp=None, stream=None):
+        """Load the lattice state from a host array (numpy / CPU tensor) or a CUDA tensor."""
+        self._spins_io(q, mp, stream, "hp_set_spins", lib().hp_set_spins)
+
+    def hp_get_spins(self, q, mp=None, stream=None):
+        """Copy the lattice state into a host array (numpy / CPU tensor) or a CUDA tensor."""
+        self._spins_io(q, mp, stream, "hp_get_spins", lib().hp_get_spins)
+
+    def _spins_io(self, q, mp, stream, w, fn):
+        host = not getattr(q, "is_cuda", False)
+        if host:
+            pq, keep_q = _host(q, self.N, np.int32, w + " q")
+            pm, keep_m = _host(mp, self.N, np.int32, w + " mp") if mp is not None else (None, None)
+            self._io_keep = (keep_q, keep_m)
+        else:
+            pq, pm = _dev(q, self.N, 4, w + " q"), _dev(mp, self.N, 4, w + " mp")
+        _check(fn(self._h, pq, pm, 1 if host else 0, _stream(stream)))
+
+    def hp_measure(self, orient_kind=None, orient=None, acc=None, stream=None):
+        """Synchronous counts / alive / texture / mean field; returns (hp_stats, hist).
+        Pass a previous (hp_stats, hist) as `acc` to add this lattice to it."""
+        kind = ORIENT_ANGLE if orient_kind is None else int(orient_kind)
+        nb = 0 if orient is None else (24 if kind == ORIENT_SO3 else 90)
+        if acc is None:
+            st, hist = hp_stats(), np.zeros(max(nb, 1), dtype=np.int64)
+        else:
+            st, hist = acc
+        if hist.size < nb or hist.dtype != np.int64:
+            raise HPError(HP_ERR_ARG, "hp_measure: histogram too small")
+        o = None if orient is None else _dev(orient, _orient_len(kind, self.n_grains), 4, "hp_measure orient")
+        _check(lib().hp_measure(self._h, kind, o, 0 if acc is None else 1, C.byref(st),
+                                hist.ctypes.data if nb else None, int(hist.size), _stream(stream)))
+        return st, hist
 
     def hp_grain_counts(self, counts, alive=None, stream=None):
         _check(lib().hp_grain_counts(self._h, _dev(counts, self.n_grains, 8, "hp_grain_counts counts"),

@@ -42,16 +42,11 @@ def cp_params_table1(e_incr, energy_scale, w_weight=1.0):
                         energy_scale=energy_scale, w_weight=w_weight)
 
 
-def _texture(torch, lat, quat, G):
-    counts = torch.empty(G, dtype=torch.int64, device="cuda")
-    alive = torch.empty(1, dtype=torch.int32, device="cuda")
-    lat.hp_grain_counts(counts, alive)
-    bins = torch.empty(2 * G, dtype=torch.int32, device="cuda")
-    hist = torch.empty(24, dtype=torch.int64, device="cuda")
-    hm.hp_texture(G, hm.ORIENT_SO3, quat, counts, bins, hist)
-    h = hist.cpu().numpy().astype(np.float64)
-    n = h[:20].sum()
-    return {"mmax_hist": h[:20] / n, "families": h[20:] / n, "alive": int(alive.item())}
+def _texture(lat, quat):
+    """hp_measure of the final lattice: SO(3) texture families, mean max Schmid
+    factor, the 24-bin histogram (counts) and grains alive."""
+    st, hist = lat.hp_measure(hm.ORIENT_SO3, quat)
+    return {"families": list(st.families), "mean_mmax": st.mean_mmax, "hist": hist, "alive": int(st.alive)}
 
 
 def run_plain(torch, cfg: HybridConfig, time_it=True):
@@ -89,16 +84,17 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
         lat.hp_sweep(cfg.refresh_every)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    tex = _texture(torch, lat, quat, cfg.G)
+    tex = _texture(lat, quat)
     lat.close()
     return {"wall_s": wall, "field_s": t_field, **tex}
 
 
 def train_surrogate(torch, prm, n_orient=65536, K=128, n_incr=20, steps=60000, lr=2e-3, seed=3000, log_every=0,
                     batch=65536):
-    """Generate samples with the MCP kernel and fit the network with the tensor-core kernels,
-    Adam on contiguous minibatches of `batch` rows taken in turn (rows are orientation-major,
-    so each minibatch holds whole orientations at every increment; batch=None uses all rows).
+    """Generate samples with the MCP kernel and fit the network with the library's training
+    loop (hp_sur_train: Adam on contiguous minibatches of `batch` rows taken in turn, cosine
+    learning-rate decay to 2 % of lr; rows are orientation-major, so each minibatch holds whole
+    orientations at every increment; batch=None uses all rows).
     Returns (params tensor, load table [n_incr, 7] (numpy), final minibatch loss, history)."""
     quat = torch.empty(n_orient, 4, dtype=torch.float32, device="cuda")
     hm.hp_orientations(n_orient, seed, hm.ORIENT_SO3, quat)
@@ -110,21 +106,13 @@ def train_surrogate(torch, prm, n_orient=65536, K=128, n_incr=20, steps=60000, l
     init = np.concatenate([p.ravel() for p in synth.mlp_init(seed + 1)]).astype(np.float32)
     params = torch.from_numpy(init).cuda()
     n = params.numel()
-    grads = torch.empty_like(params)
     m = torch.zeros(n, device="cuda")
     v = torch.zeros(n, device="cuda")
     loss = torch.zeros(1, device="cuda")
-    hist = []
-    B = M if batch is None else min(int(batch) // n_incr * n_incr, M)
-    n_batches = max(1, M // B)
-    for step in range(1, steps + 1):
-        lr_t = lr * (0.02 + 0.98 * 0.5 * (1 + np.cos(np.pi * step / steps)))  # cosine decay
-        r0 = ((step - 1) % n_batches) * B
-        hm.hp_mlp_gradients(params, X[r0:r0 + B], Y[r0:r0 + B], grads, loss)
-        hm.hp_mlp_adam(params, grads, m, v, step, lr_t)
-        if log_every and step % log_every == 0:
-            hist.append((step, float(loss.item())))
+    log = hm.hp_sur_train(params, m, v, X, Y, steps, batch=batch or 0, group=n_incr, lr=lr, lr_floor=0.02,
+                          loss=loss, log_every=log_every)
     torch.cuda.synchronize()
+    hist = [((i + 1) * log_every, float(x)) for i, x in enumerate(log)]
     return params, load.cpu().numpy(), float(loss.item()), hist
 
 
@@ -156,6 +144,6 @@ def run_surrogate(torch, cfg: HybridConfig, params, load_table, time_it=True):
         lat.hp_sweep(cfg.refresh_every)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    tex = _texture(torch, lat, quat, cfg.G)
+    tex = _texture(lat, quat)
     lat.close()
     return {"wall_s": wall, "field_s": t_field, **tex}

@@ -36,9 +36,6 @@ def run_gaussian_2d(torch, R=100, L=(500, 500), G=5000, kT=1.0, slices=(0, 100, 
         members.append(lat)
         keep.append((q, ang, b))
     ens = hm.Ensemble(members)
-    counts = torch.empty(G, dtype=torch.int64, device="cuda")
-    bins = torch.empty(G, dtype=torch.int32, device="cuda")
-    hist = torch.empty(90, dtype=torch.int64, device="cuda")
     out = {"slices": list(slices), "hist": [], "mean_b": []}
     t0 = time.perf_counter()
     done = 0
@@ -46,15 +43,11 @@ def run_gaussian_2d(torch, R=100, L=(500, 500), G=5000, kT=1.0, slices=(0, 100, 
         if t > done:
             ens.hp_ensemble_sweep(t - done)
             done = t
-        tot = np.zeros(90)
-        sb = 0.0
-        for lat, (q, ang, b) in zip(members, keep):
-            lat.hp_grain_counts(counts)
-            hm.hp_texture(G, hm.ORIENT_ANGLE, ang, counts, bins, hist)
-            tot += hist.cpu().numpy()
-            sb += float((counts.double() * b.double()).sum().item())
-        out["hist"].append(tot)
-        out["mean_b"].append(sb / tot.sum() / 256.0)
+        acc = None
+        for lat, (q, ang, b) in zip(members, keep):  # one hp_stats gathers the whole ensemble
+            acc = lat.hp_measure(hm.ORIENT_ANGLE, ang, acc=acc)
+        out["hist"].append(acc[1].copy())
+        out["mean_b"].append(acc[0].mean_field)
     torch.cuda.synchronize()
     out["seconds"] = time.perf_counter() - t0
     ens.close()
@@ -83,15 +76,10 @@ def run_plastic_3d(torch, L=(128, 128, 128), G=4000, seed=11, kT=2.6, n_incr=100
     thr, D = hm.hp_build_threshold_table(kT)
     lat.hp_set_threshold_table(thr, D)
     lat.hp_set_field(b)
-    counts = torch.empty(G, dtype=torch.int64, device="cuda")
-    bins = torch.empty(G, dtype=torch.int32, device="cuda")
-    hist = torch.empty(90, dtype=torch.int64, device="cuda")
     out = {"t": [], "g": [], "hist": []}
 
     def measure(t):
-        lat.hp_grain_counts(counts)
-        hm.hp_texture(G, hm.ORIENT_ZROT, quat, counts, bins, hist)
-        h = hist.cpu().numpy()
+        _, h = lat.hp_measure(hm.ORIENT_ZROT, quat)
         out["t"].append(t)
         out["g"].append(hm.hp_texture_fit(h)[0])
         out["hist"].append(h)

@@ -54,3 +54,52 @@ def test_bad_arguments_are_rejected(hm):
     with pytest.raises(hm.HPError) as e:
         lat.hp_sweep(1, stream=0)
     assert e.value.code == hm.HP_ERR_STATE
+
+
+def test_last_error_copies_the_message(hm):
+    with pytest.raises(hm.HPError):
+        hm.Lattice(2, (7, 8), 8, 256, 1, 4)
+    msg = hm.hp_last_error()
+    assert "even" in msg
+    import ctypes as C
+    buf = C.create_string_buffer(6)
+    assert hm.lib().hp_last_error(None, buf, 6) == hm.HP_OK
+    assert buf.value.decode() == msg[:5]
+    assert hm.lib().hp_last_error(None, None, 8) == hm.HP_ERR_ARG
+
+
+def test_state_and_argument_errors_of_io_and_measure(hm):
+    """Calls on a handle with nothing bound fail before touching the device."""
+    lat = hm.Lattice(2, (8, 8), 8, 256, 1, 4)
+    q = np.zeros(64, dtype=np.int32)
+    with pytest.raises(hm.HPError) as e:
+        lat.hp_set_spins(q, stream=0)
+    assert e.value.code == hm.HP_ERR_STATE
+    with pytest.raises(hm.HPError) as e:
+        lat.hp_get_spins(q, stream=0)
+    assert e.value.code == hm.HP_ERR_STATE
+    with pytest.raises(hm.HPError) as e:
+        lat.hp_measure(stream=0)
+    assert e.value.code == hm.HP_ERR_STATE
+    # the binding refuses short or mistyped host buffers
+    with pytest.raises(hm.HPError) as e:
+        lat.hp_set_spins(np.zeros(63, dtype=np.int32), stream=0)
+    assert e.value.code == hm.HP_ERR_ARG
+    with pytest.raises(hm.HPError):
+        lat.hp_set_spins(np.zeros(64, dtype=np.int64), stream=0)
+    assert hm.lib().hp_measure(None, 0, None, 0, None, None, 0, None) == hm.HP_ERR_ARG
+
+
+def test_sur_train_argument_errors(hm):
+    """hp_sur_train validates its schedule before any device work."""
+    import ctypes as C
+    tp = hm.hp_sur_train_params(10, 0, 0, 1e-3, 0.02, 0.9, 0.999, 1e-8, 0)  # group 0
+    dummy = C.c_void_p(16)
+    rc = hm.lib().hp_sur_train(dummy, dummy, dummy, dummy, dummy, 100, C.byref(tp), 0, None, None, None)
+    assert rc == hm.HP_ERR_ARG
+    tp = hm.hp_sur_train_params(10, 0, 1, 1e-3, 1.5, 0.9, 0.999, 1e-8, 0)  # floor above 1
+    assert hm.lib().hp_sur_train(dummy, dummy, dummy, dummy, dummy, 100, C.byref(tp), 0, None, None, None) == \
+        hm.HP_ERR_ARG
+    tp = hm.hp_sur_train_params(10, 0, 1, 1e-3, 0.02, 0.9, 0.999, 1e-8, 5)  # a log without a host array
+    assert hm.lib().hp_sur_train(dummy, dummy, dummy, dummy, dummy, 100, C.byref(tp), 0, None, None, None) == \
+        hm.HP_ERR_ARG

@@ -94,9 +94,9 @@ def test_sweep_zero_mcs_is_noop():
     np.testing.assert_array_equal(q, q0)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_sweep_full_size_2d_moore_two_mcs(oracle, variant):
-    """4096^2 Moore lattice, 10^4 grains, grain field: 2 MCS bit-exact (plane, TMA-fed and strip variants)."""
+    """4096^2 Moore lattice, 10^4 grains, grain field: 2 MCS bit-exact (plane and lean tile variants)."""
     torch, hm = need_gpu()
     L, G = (4096, 4096), 10_000
     q0 = synth.blocky_lattice(L, G, 5, block=40)
@@ -109,7 +109,7 @@ def test_sweep_full_size_2d_moore_two_mcs(oracle, variant):
     assert hm.hp_sweep_status() == 0
 
 
-@pytest.mark.parametrize("variant", [2, 4, 6, 7, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("variant", [2, 4, 5, 6, 7, 8, 9])
 def test_sweep_full_size_3d_point_field_one_mcs(oracle, variant):
     """512^3 26-neighbour lattice with a per-material-point field: one MCS bit-exact."""
     torch, hm = need_gpu()
@@ -127,7 +127,7 @@ def test_sweep_full_size_3d_point_field_one_mcs(oracle, variant):
 
 
 @pytest.mark.parametrize("kind", ["monotone", "perturbed"])
-@pytest.mark.parametrize("variant", [0, 10])
+@pytest.mark.parametrize("variant", [0, 4])
 def test_sweep_arbitrary_threshold_table(oracle, kind, variant):
     """The threshold table is input data: a table that is not of the exp form (any
     monotone table, or an exp table with one entry moved) gives the oracle's

@@ -151,6 +151,8 @@ CASES = [
     ((136, 72), 4, (128, 60)), ((132, 130), 4, (64, 60)), ((4, 4), 4, (128, 28)),
     ((200, 130), 8, (128, 60)), ((250, 62), 8, (128, 28)), ((128, 128), 8, (64, 60)), ((66, 2), 8, (128, 60)),
     ((70, 40, 4), 26, (64, 36)), ((136, 40, 4), 26, (128, 28)), ((64, 74, 4), 26, (64, 28)), ((12, 10, 4), 26, (64, 60)),
+    # the lean 3D kernel's windows (64 x 44, core 56 x 40; 64 x 40, core 56 x 36) follow the same schedule
+    ((120, 86, 4), 26, (64, 40)), ((64, 44, 4), 26, (64, 40)), ((118, 74, 4), 26, (64, 36)),
 ]
 
 
