@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Benchmark: Potts site-updates/s of the hybrid Monte Carlo hot path on GB300.
 
-Workload (default): 2D 4096x4096 periodic lattice, Moore 8-neighbour 4-colour
-sweep, 10^4 Voronoi grains with SO(3)-uniform cubic-Ni orientations, per-grain
-field = elastic energy under uniaxial 100 MPa + dislocation energy weighted by
-the max Schmid factor, kT = 0.6, 1000 MCS.  One step = the whole job on
-synthetic input already in HBM: Voronoi initialisation, closed-form field,
-1000 MCS, grain counts and texture histogram.
+Workload (default): the 3D 1024^3 periodic simple cubic lattice, 26-neighbour
+8-colour sweep, 10^6 Voronoi grains of FCC nickel with SO(3)-uniform
+orientations, driven by the per-material-point field of the Monte Carlo crystal
+plasticity (Table 1 constants, Taylor increment 1e-4), kT = 0.7, refreshed every
+50 MCS by two increments (the plain-solver arm of the 1024^3 surrogate-vs-plain
+configuration).  One step = one refresh period on the device-resident state:
+the plasticity update of every material point (two increments, new field)
+followed by 50 MCS of the sweep.  The line also carries the time to texture
+(500 MCS) of the plain and the surrogate-driven hybrids at the same size.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload ...]
 
 Prints ONE JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
 rank runs its own independent lattice (its own seed): weak scaling, no
@@ -18,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mproc
 import os
 import statistics
 import subprocess
@@ -31,8 +35,10 @@ import numpy as np  # noqa: E402
 
 from paper_1007_3509_gb300 import synth  # noqa: E402
 
-W = synth.W2D_MOORE
-BYTES_PER_SITE_UPDATE = 8  # q read + q write per site per MCS; field looked up per grain (L1/L2)
+W4 = synth.W3D_SURROGATE          # 1024^3, 10^6 grains, kT 0.7, refresh every 50 MCS
+W = synth.W2D_MOORE               # 4096^2 Moore: secondary line (L2-assisted)
+BYTES_3D_POINT = 24               # q, b, mp read and written once per site-update
+BYTES_2D_GRAIN = 8                # q read and written; the per-grain field from L1/L2
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -45,19 +51,22 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--no-texture", action="store_true", help="skip the time-to-texture runs of both arms")
     p.add_argument("--mcs", type=int, default=None, help="MCS per step (default: the workload's)")
     p.add_argument("--variant", type=int, default=None, help="fused-sweep tile variant (default: autotuned)")
-    p.add_argument("--workload", choices=["2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
-                                          "texture3d"], default="2d",
-                   help="2d: 4096^2 Moore (default line); 3d-cp: 512^3 plasticity-driven hybrid; ensemble: 256 "
-                        "replicas; surrogate: 1024^3 plain vs surrogate time-to-texture")
-    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--edge", type=int, default=None,
-                   help="3d-cp: lattice edge (default 512); grains scale with the volume")
+                   help="3D workloads: lattice edge (default 1024, or 512 for 3d-cp); grains scale with the volume")
+    p.add_argument("--workload", choices=["3d", "2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
+                                          "texture3d", "texture-seeds"], default="3d",
+                   help="3d: 1024^3 plasticity-driven hybrid (default line); 2d: 4096^2 Moore; 3d-cp: 512^3 "
+                        "plasticity-driven whole job; ensemble: 256 replicas; surrogate: 1024^3 plain vs surrogate "
+                        "time-to-texture; texture-seeds: both arms over 8 seeds each")
+    p.add_argument("--seeds", type=int, default=8, help="texture-seeds: seeds per arm")
+    p.add_argument("--no-autotune", action="store_true")
     a = p.parse_args()
     if a.mcs is None:
-        a.mcs = {"2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20, "texture2d": 1000,
-                 "texture3d": 400}[a.workload]
+        a.mcs = {"3d": 50, "2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20,
+                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500}[a.workload]
     return a
 
 
@@ -119,177 +128,8 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------------------
-# our arm
-# ---------------------------------------------------------------------------
-class Job:
-    """Device-resident buffers of one lattice of the workload."""
-
-    def __init__(self, torch, hm, seed, mcs):
-        self.torch, self.hm, self.mcs = torch, hm, mcs
-        L, G = W.L, W.G
-        self.N = int(np.prod(L))
-        dev = "cuda"
-        self.lat = hm.Lattice(2, L, W.nbr, int(256 * W.J), seed, G, hm.FIELD_GRAIN)
-        self.q = torch.empty(self.N, dtype=torch.int32, device=dev)
-        self.lat.hp_bind(self.q)
-        self.quat = torch.empty(G, 4, dtype=torch.float32, device=dev)
-        self.bgrain = torch.empty(G, dtype=torch.int32, device=dev)
-        self.counts = torch.empty(G, dtype=torch.int64, device=dev)
-        self.alive = torch.empty(1, dtype=torch.int32, device=dev)
-        self.bins = torch.empty(2 * G, dtype=torch.int32, device=dev)
-        self.hist = torch.empty(24, dtype=torch.int64, device=dev)
-        thr, D = hm.hp_build_threshold_table(W.kT)
-        self.lat.hp_set_threshold_table(thr, D)
-        self.lat.hp_set_field(self.bgrain)
-        self.C = [synth.NI_BJ[k] for k in ("C11", "C12", "C44")]
-        self.tuned = None
-
-    def autotune(self):
-        """Pick the fastest tile shape on the initialised lattice (state restored)."""
-        self.lat.hp_init_voronoi(self.hm.ORIENT_SO3, self.quat)
-        self.field()
-        chosen, ms = self.lat.hp_sweep_autotune(8)
-        self.tuned = {"variant": int(chosen), "ms_per_8_mcs": [round(float(x), 3) for x in ms]}
-
-    def field(self):
-        self.hm.hp_grain_field(self.quat, *self.C, W.sigma, W.k_disl, W.energy_scale, self.bgrain)
-
-    def measure(self):
-        self.lat.hp_grain_counts(self.counts, self.alive)
-        self.hm.hp_texture(W.G, self.hm.ORIENT_SO3, self.quat, self.counts, self.bins, self.hist)
-
-    def step(self, ev_sweep=None):
-        """Whole job: init, field, sweep, measure."""
-        self.lat.hp_init_voronoi(self.hm.ORIENT_SO3, self.quat)
-        self.field()
-        self.lat.hp_set_sweep_counter(0)
-        if ev_sweep:
-            ev_sweep[0].record()
-        self.lat.hp_sweep(self.mcs)
-        if ev_sweep:
-            ev_sweep[1].record()
-        self.measure()
-
-
-# algorithmic bytes per site-update of the 3D per-material-point-field sweep:
-# the per-site state (grain id q, stored energy b, material point mp) read and
-# written once per MCS
-BYTES_3D_POINT = 24
-
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, ncu capture of the
-# 4096^2 Moore workload, keyed by (neighbours, tile variant)
-MEASURED_TRAFFIC = {(8, 10): 67.998208e6 + 19.811072e6}
-
-
-def sweep_kernel_name(nbr, variant):
-    """Kernel family of a fused-sweep tile variant (variant numbering of hp_sweep_variants)."""
-    v = int(variant or 0)
-    plane_n = 6 if nbr == 26 else 5
-    strip_end = 9
-    if v < plane_n:
-        kind = "k_plane_tma" if (v >= plane_n - 2) else "k_plane"
-    elif v < strip_end:
-        kind = "k_strip"
-    else:
-        kind = "k_tile"
-    return f"{kind}<{nbr}> (fused MCS, variant {v})"
-
-
-def run_ours(args, rank, world, local_rank):
-    import torch
-    from paper_1007_3509_gb300 import build, hmcpotts as hm
-    torch.cuda.set_device(local_rank)
-    if rank == 0:
-        build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    hm.lib()
-    job = Job(torch, hm, W.seed + rank, args.mcs)
-    if args.variant is not None:
-        job.lat.hp_set_sweep_variant(args.variant)
-        job.tuned = {"variant": int(args.variant), "ms_per_8_mcs": None}
-    elif not args.no_autotune:
-        job.autotune()
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-    for _ in range(args.warmup):
-        job.step()
-    torch.cuda.synchronize()
-
-    clocks = Clocks(local_rank)
-    launches0 = hm.hp_kernel_launches()
-    step_ms, sweep_ms = [], []
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for _ in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the events)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        job.step((s0, s1))
-        e1.record()
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        sweep_ms.append(s0.elapsed_time(s1))
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    launches = hm.hp_kernel_launches() - launches0
-    total_ms = sum(step_ms)
-    max_ms, value = aggregate(total_ms, job.N * args.mcs * args.steps, world, "cuda")
-
-    # dominant kernel: one fused-plane launch per MCS over N sites
-    per_launch_s = statistics.mean(sweep_ms) / 1e3 / args.mcs
-    achieved = BYTES_PER_SITE_UPDATE * job.N / per_launch_s / 1e9
-    peak, peak_kind = peaks()
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-            "kernel": sweep_kernel_name(W.nbr, job.tuned.get("variant") if job.tuned else 0),
-            "bytes_per_site_update": BYTES_PER_SITE_UPDATE,
-            "sweep_site_updates_per_s": round(job.N / per_launch_s, 1)}
-    # DRAM bytes of one launch of the kernel, from an ncu capture of that exact
-    # variant (profiles/k_tile8_2d4096_moore.md); null for any other kernel
-    traffic = MEASURED_TRAFFIC.get((W.nbr, job.tuned.get("variant") if job.tuned else None))
-    if traffic is not None:
-        roof["traffic"] = traffic
-
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(torch, hm, job, args)
-    secondary = None
-    if not args.no_secondary and rank == 0:
-        secondary = run_secondary(torch, hm)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample(target_s=12.0)
-    if rank != 0:
-        return
-    line = {
-        "metric": "Potts site-updates/s",
-        "value": round(value, 1),
-        "unit": "site-updates/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(max_ms / args.steps, 3),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "int32",
-        "data": "synthetic (seeded Voronoi polycrystal, SO(3)-uniform orientations)",
-        "config": {"workload": W.name, "lattice": list(W.L), "nbr": W.nbr, "colours": 4, "grains": W.G,
-                   "kT": W.kT, "mcs_per_step": args.mcs, "field": "per-grain closed form (100 MPa, Ni)",
-                   "step": "voronoi init + field + sweep + counts/texture", "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}", "tile": job.tuned},
-        "roofline": roof,
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "gpu_launches": launches,
-        "clocks": clk,
-        "secondary": secondary,
-    }
-    print(json.dumps(line))
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
 def aggregate(local_ms, local_units, world, device):
@@ -304,82 +144,297 @@ def aggregate(local_ms, local_units, world, device):
     return max_ms, local_units * world / (max_ms / 1e3)
 
 
+# ---------------------------------------------------------------------------
+# our arm: the 3D plasticity-driven hybrid
+# ---------------------------------------------------------------------------
+def shape3d(edge):
+    """Lattice, grain count (10^6 at 1024^3, same mean grain volume at other edges)."""
+    e = int(edge or W4.L[0])
+    N = e ** 3
+    return (e, e, e), N, max(1, round(W4.G * N / W4.N))
+
+
+class Hybrid3D:
+    """Device-resident state of the plasticity-driven 3D hybrid (one lattice)."""
+
+    def __init__(self, torch, hm, hybrid, edge, seed):
+        self.torch, self.hm = torch, hm
+        ex = W4.extra
+        self.L, self.N, self.G = shape3d(edge)
+        self.seed = seed
+        self.every, self.incr_per = ex["refresh_every"], ex["incr_per_refresh"]
+        self.prm = hybrid.cp_params_table1(ex["e_incr"], ex["energy_scale"])
+        N, dev = self.N, "cuda"
+        self.lat = hm.Lattice(3, self.L, 26, 256, seed, self.G, hm.FIELD_POINT)
+        self.q = torch.empty(N, dtype=torch.int32, device=dev)
+        self.mp = torch.empty(N, dtype=torch.int32, device=dev)
+        self.lat.hp_bind(self.q, self.mp)
+        self.quat = torch.empty(self.G, 4, dtype=torch.float32, device=dev)
+        self.eps = torch.empty(6 * N, dtype=torch.float32, device=dev)
+        self.gam = torch.empty(N, dtype=torch.float32, device=dev)
+        self.g = torch.empty(N, dtype=torch.float32, device=dev)
+        self.b = torch.empty(N, dtype=torch.int32, device=dev)
+        thr, D = hm.hp_build_threshold_table(W4.kT)
+        self.lat.hp_set_threshold_table(thr, D)
+        self.lat.hp_set_field(self.b)
+        self.tuned = None
+        self.reset()
+
+    def reset(self):
+        """Voronoi polycrystal, material point p in the grain of site p, no plastic strain."""
+        self.lat.hp_init_voronoi(self.hm.ORIENT_SO3, self.quat)
+        self.grain = self.q.clone()
+        self.hm.hp_cp_reset(self.prm, self.N, self.eps, self.gam, self.g)
+        self.lat.hp_set_sweep_counter(0)
+        self.incr = 0
+
+    def autotune(self):
+        """Pick the fastest sweep tile on the current lattice (lattice and counter restored)."""
+        self.refresh()
+        chosen, ms = self.lat.hp_sweep_autotune(2)
+        self.tuned = {"variant": int(chosen), "ms_per_2_mcs": [round(float(x), 3) for x in ms]}
+        self.reset()
+
+    def refresh(self):
+        self.hm.hp_cp_step(self.prm, self.seed, self.grain, self.quat, self.incr, self.incr_per, self.eps, self.gam,
+                           self.g, b=self.b)
+        self.incr += self.incr_per
+
+    def step(self, ev=None):
+        """One refresh period: plasticity update (new field), then `every` MCS."""
+        if ev:
+            ev[0].record()
+        self.refresh()
+        if ev:
+            ev[1].record()
+        self.lat.hp_sweep(self.every)
+        if ev:
+            ev[2].record()
+
+    def close(self):
+        self.lat.close()
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the 3D sweep
+# kernel (one plane parity of the 1024^3 lattice, the point-field lean window),
+# from an ncu capture of that exact kernel; keyed by tile variant.  None for any
+# other kernel or once the kernel has changed since the capture.
+MEASURED_TRAFFIC_3D = {}
+
+
+def sweep_kernel_name(nbr, variant):
+    """Kernel family of a fused-sweep tile variant (numbering of hp_sweep_variants)."""
+    v = int(variant or 0)
+    if nbr == 26:
+        kind = "k_plane" if v < 4 else ("k_tile" if v < 8 else "k_lean26")
+    else:
+        kind = "k_plane" if v < 3 else "k_tile"
+    return f"{kind}<{nbr}> (fused MCS, variant {v})"
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm, hybrid
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    hm.lib()
+    job = Hybrid3D(torch, hm, hybrid, args.edge, W4.seed + rank)
+    job.every = args.mcs
+    if args.variant is not None:
+        job.lat.hp_set_sweep_variant(args.variant)
+        job.tuned = {"variant": int(args.variant), "ms_per_2_mcs": None}
+    elif not args.no_autotune:
+        job.autotune()
+    for _ in range(args.warmup):
+        job.step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local_rank)
+    launches0 = hm.hp_kernel_launches()
+    step_ms, cp_ms, sweep_ms = [], [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        e0, e1 = _events(torch)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+              torch.cuda.Event(enable_timing=True))
+        e0.record()
+        job.step(ev)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        cp_ms.append(ev[0].elapsed_time(ev[1]))
+        sweep_ms.append(ev[1].elapsed_time(ev[2]))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = hm.hp_kernel_launches() - launches0
+    total_ms = sum(step_ms)
+    max_ms, value = aggregate(total_ms, job.N * job.every * args.steps, world, "cuda")
+
+    # dominant kernel: the sweep, two launches per MCS (even then odd planes),
+    # each over N/2 site-updates of 24 algorithmic bytes
+    launch_s = statistics.mean(sweep_ms) / 1e3 / (2 * job.every)
+    achieved = BYTES_3D_POINT * (job.N / 2) / launch_s / 1e9
+    peak, peak_kind = peaks()
+    variant = job.tuned.get("variant") if job.tuned else None
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": MEASURED_TRAFFIC_3D.get(variant),
+            "peak_source": peak_kind, "kernel": sweep_kernel_name(26, variant),
+            "bytes_per_site_update": BYTES_3D_POINT, "site_updates_per_launch": job.N // 2,
+            "launch_ms": round(launch_s * 1e3, 4),
+            "sweep_site_updates_per_s": round(job.N / (2 * launch_s), 1),
+            "share_of_step": round(sum(sweep_ms) / total_ms, 4)}
+    plast = {"point_increments_per_s": round(job.N * job.incr_per / (statistics.mean(cp_ms) / 1e3), 1),
+             "ms_per_refresh": round(statistics.mean(cp_ms), 3), "share_of_step": round(sum(cp_ms) / total_ms, 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(torch, hm, job, args)
+    tuned = job.tuned
+    job.close()
+    del job
+    torch.cuda.empty_cache()
+    ttt = None
+    if not args.no_texture and rank == 0 and world == 1:
+        ttt = time_to_texture(torch, hm, hybrid, args)
+    secondary = None
+    if not args.no_secondary and rank == 0:
+        secondary = {"2d_4096_moore_L2_assisted": run_2d_secondary(torch, hm)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(args)
+    if rank != 0:
+        return
+    L, N, G = shape3d(args.edge)
+    line = {
+        "metric": "Potts site-updates/s",
+        "value": round(value, 1),
+        "unit": "site-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(max_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32 sweep; fp32 plasticity with fp64 return map",
+        "data": "synthetic (seeded Voronoi polycrystal, SO(3)-uniform FCC Ni orientations)",
+        "config": {"workload": f"3d-{L[0]}-moore26-g{G}-plain-mcp-hybrid", "lattice": list(L), "nbr": 26,
+                   "colours": 8, "grains": G, "kT": W4.kT, "mcs_per_step": args.mcs,
+                   "field": "per material point: MCP (Table 1 Ni), 2 Taylor increments of 1e-4 per step",
+                   "step": "MCP refresh of every material point + 50 MCS", "l2": "inputs larger than L2 (4 GB per array)",
+                   "parallelism": f"replicas x{world}", "tile": tuned},
+        "roofline": roof,
+        "plasticity": plast,
+        "time_to_texture": ttt,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "secondary": secondary,
+    }
+    print(json.dumps(line))
+
+
 def run_e2e(torch, hm, job, args):
-    """Same metric through the public API with host buffers: pinned H2D of the
-    initial lattice and orientations, field + sweep + measure, D2H of the final
-    lattice, counts and histogram, every step."""
-    G, N = W.G, job.N
-    job.lat.hp_init_voronoi(hm.ORIENT_SO3, job.quat)
-    h_q = job.q.cpu().pin_memory()
-    h_quat = job.quat.cpu().pin_memory()
-    o_q = torch.empty(N, dtype=torch.int32).pin_memory()
-    o_counts = torch.empty(G, dtype=torch.int64).pin_memory()
-    o_hist = torch.empty(24, dtype=torch.int64).pin_memory()
+    """The same step through the public C ABI with host buffers: the lattice state
+    (q, mp) goes in from pinned host memory (hp_set_spins), the plasticity refresh
+    and the 50 MCS run, and the state (hp_get_spins) and the grain statistics and
+    texture (hp_measure) come back to the host, every step."""
+    N = job.N
+    h_q = torch.empty(N, dtype=torch.int32).pin_memory()
+    h_mp = torch.empty(N, dtype=torch.int32).pin_memory()
+    job.lat.hp_get_spins(h_q, h_mp)
+    torch.cuda.synchronize()
 
     def one():
-        job.q.copy_(h_q, non_blocking=True)
-        job.quat.copy_(h_quat, non_blocking=True)
-        job.field()
-        job.lat.hp_set_sweep_counter(0)
-        job.lat.hp_sweep(args.mcs)
-        job.measure()
-        o_q.copy_(job.q, non_blocking=True)
-        o_counts.copy_(job.counts, non_blocking=True)
-        o_hist.copy_(job.hist, non_blocking=True)
+        job.lat.hp_set_spins(h_q, h_mp)
+        job.step()
+        job.lat.hp_get_spins(h_q, h_mp)
+        st, hist = job.lat.hp_measure(hm.ORIENT_SO3, job.quat)  # synchronises
+        return st
 
     one()
     torch.cuda.synchronize()
     ms = []
     steps = max(2, min(args.steps, 3))
     for _ in range(steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record()
         one()
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     per = statistics.mean(ms) / 1e3
-    h2d = h_q.numel() * 4 + h_quat.numel() * 4
-    d2h = o_q.numel() * 4 + o_counts.numel() * 8 + o_hist.numel() * 8
-    return {"value": round(N * args.mcs / per, 1), "unit": "site-updates/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": round(per * 1e3, 3)}
+    return {"value": round(N * job.every / per, 1), "unit": "site-updates/s", "h2d_bytes_per_step": 8 * N,
+            "d2h_bytes_per_step": 8 * N + 24 * 8, "ms_per_step": round(per * 1e3, 3),
+            "path": "hp_set_spins (host) + hp_cp_step + hp_sweep + hp_get_spins (host) + hp_measure"}
 
 
-def run_secondary(torch, hm):
-    """The 3D 512^3 26-neighbour 8-colour sweep with a per-material-point field
-    (two fused launches per MCS), for the HBM roofline of the 3D path."""
+def time_to_texture(torch, hm, hybrid, args):
+    """Wall time to 500 MCS of both arms at the bench size from a fresh polycrystal:
+    the plain hybrid (plasticity at every material point each refresh) and the
+    surrogate-driven one (its training data generated and the network trained in
+    the timed region, then one network evaluation per grain each refresh)."""
+    L, N, G = shape3d(args.edge)
+    cfg = hybrid.HybridConfig(L=L, G=G, seed=W4.seed, kT=W4.kT, n_mcs=500)
+    prm = hybrid.cp_params_table1(cfg.e_incr, cfg.energy_scale)
+    plain = hybrid.run_plain(torch, cfg, time_it=False)
+    torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    params, load, loss, _ = hybrid.train_surrogate(torch, prm)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    sur = hybrid.run_surrogate(torch, cfg, params, load, time_it=False)
+    torch.cuda.empty_cache()
+    return {"mcs": 500, "plain_s": round(plain["wall_s"], 3), "surrogate_s": round(train_s + sur["wall_s"], 3),
+            "surrogate_train_s": round(train_s, 3), "surrogate_run_s": round(sur["wall_s"], 3),
+            "speedup": round(plain["wall_s"] / (train_s + sur["wall_s"]), 3),
+            "families_plain": [round(x, 5) for x in plain["families"]],
+            "families_surrogate": [round(x, 5) for x in sur["families"]],
+            "mean_mmax_plain": round(plain["mean_mmax"], 5), "mean_mmax_surrogate": round(sur["mean_mmax"], 5),
+            "seeds_per_arm": 1, "final_train_loss": loss}
+
+
+def run_2d_secondary(torch, hm):
+    """The 2D 4096^2 Moore sweep with the closed-form per-grain field (1000 MCS of
+    the lean tile kernel): partly L2-resident, not an HBM figure."""
     try:
-        L = (512, 512, 512)
-        N = 512 ** 3
-        lat = hm.Lattice(3, L, 26, 256, 1002, 200_000, hm.FIELD_POINT)
+        L, G = W.L, W.G
+        N = int(np.prod(L))
+        lat = hm.Lattice(2, L, W.nbr, int(256 * W.J), W.seed, G, hm.FIELD_GRAIN)
         q = torch.empty(N, dtype=torch.int32, device="cuda")
-        mp = torch.empty(N, dtype=torch.int32, device="cuda")
-        lat.hp_bind(q, mp)
-        lat.hp_init_voronoi(hm.ORIENT_SO3, None)
-        bmp = torch.randint(0, 30, (N,), dtype=torch.int32, device="cuda")
-        lat.hp_set_field(bmp)
-        thr, D = hm.hp_build_threshold_table(0.7)
-        lat.hp_set_threshold_table(thr, D)
-        chosen, ms = lat.hp_sweep_autotune(4)
-        lat.hp_sweep(4)
+        lat.hp_bind(q)
+        quat = torch.empty(G, 4, dtype=torch.float32, device="cuda")
+        bg = torch.empty(G, dtype=torch.int32, device="cuda")
+        lat.hp_init_voronoi(hm.ORIENT_SO3, quat)
+        hm.hp_grain_field(quat, *[synth.NI_BJ[k] for k in ("C11", "C12", "C44")], W.sigma, W.k_disl,
+                          W.energy_scale, bg)
+        lat.hp_set_field(bg)
+        lat.hp_set_threshold_table(*hm.hp_build_threshold_table(W.kT))
+        chosen, _ = lat.hp_sweep_autotune(8)
+        lat.hp_sweep(20)
         torch.cuda.synchronize()
-        n = 20
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch)
         e0.record()
-        lat.hp_sweep(n)
+        lat.hp_sweep(W.n_mcs)
         e1.record()
         torch.cuda.synchronize()
         s = e0.elapsed_time(e1) / 1e3
-        rate = N * n / s
-        bytes_per = BYTES_3D_POINT
         peak, _ = peaks()
+        rate = N * W.n_mcs / s
         lat.close()
-        del q, mp, bmp
-        torch.cuda.empty_cache()
-        return {"workload": "3d-512-moore26-point-field", "site_updates_per_s": round(rate, 1),
-                "bytes_per_site_update": bytes_per, "achieved_gbs": round(rate * bytes_per / 1e9, 1),
-                "frac_of_measured_hbm": round(rate * bytes_per / 1e9 / peak, 4), "mcs_timed": n,
-                "tile": {"variant": int(chosen), "ms_per_4_mcs": [round(float(x), 3) for x in ms]}}
+        return {"workload": W.name, "site_updates_per_s": round(rate, 1), "mcs": W.n_mcs,
+                "kernel": sweep_kernel_name(W.nbr, chosen), "bytes_per_site_update": BYTES_2D_GRAIN,
+                "achieved_gbs": round(rate * BYTES_2D_GRAIN / 1e9, 1),
+                "frac_of_measured_hbm": round(rate * BYTES_2D_GRAIN / 1e9 / peak, 4),
+                "note": "two 64 MB lattices, partly L2-resident"}
     except Exception as e:  # secondary numbers must not break the main line
         return {"error": str(e)[:200]}
 
@@ -387,57 +442,90 @@ def run_secondary(torch, hm):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_job(L, G, mcs, seed):
-    """The oracle running the same job on a smaller lattice of the same grain
-    density: Voronoi, closed-form field, mcs Monte Carlo steps, counts."""
+SAMPLE_EDGE = 56   # 3D sample of the bench workload family: same mean grain volume (about 1074 sites)
+
+
+def oracle_job3d(edge, mcs, seed, n_refresh=1):
+    """The oracle running the bench's job on an edge^3 lattice of the same grain
+    density: Voronoi, then n_refresh periods of (2 plasticity increments at every
+    material point, the Eq. (4) field, `mcs` Monte Carlo steps), then grain counts.
+    Returns (site-updates, seconds)."""
     import oracle
     t0 = time.perf_counter()
-    q, _ = oracle.voronoi(2, L, G, seed)
+    L = (edge, edge, edge)
+    N = edge ** 3
+    G = max(1, round(W4.G * N / W4.N))
+    ex = W4.extra
+    q, _ = oracle.voronoi(3, L, G, seed)
     quat = oracle.orientations(G, seed, 1)
-    Cc = np.array([synth.NI_BJ[k] for k in ("C11", "C12", "C44")])
-    _, _, _, b = oracle.grain_field(quat, Cc, W.sigma, W.k_disl, W.energy_scale)
-    thr, D = oracle.threshold_table(W.kT)
-    q2, _, _, _ = oracle.sweep(2, L, W.nbr, int(256 * W.J), seed, 0, mcs, thr, D, q, b[q], None)
-    counts, alive = oracle.grain_counts(q2, G)
-    bins, _ = oracle.grain_bins(quat, 1)
-    oracle.histogram(counts, bins, 1)
+    c = synth.TABLE1
+    P = oracle.cp_params(c["C11"], c["C12"], c["C44"], c["tau0"], c["taus"], c["h0"], c["beta"], ex["e_incr"])
+    grain = q.copy()
+    mp = np.arange(N, dtype=np.int32)
+    ep = np.zeros((N, 6))
+    gm = np.zeros(N)
+    thr, D = oracle.threshold_table(W4.kT)
+    sweep0 = 0
+    for r in range(n_refresh):
+        ep, gm, sg, _, _ = oracle.mcp_run(P, seed, grain, quat, r * ex["incr_per_refresh"], ex["incr_per_refresh"], ep,
+                                          gm)
+        w, er = oracle.mcp_energies(P, sg, gm)
+        bmp = oracle.quantise(ex["energy_scale"] * (w + er))
+        q, _, mp, _ = oracle.sweep(3, L, 26, 256, seed, sweep0, mcs, thr, D, q, bmp[mp], mp)
+        sweep0 += mcs
+    oracle.grain_counts(q, G)
+    return N * mcs * n_refresh, time.perf_counter() - t0
+
+
+def _oracle_worker(a):
+    edge, mcs, seed = a
+    return oracle_job3d(edge, mcs, seed)
+
+
+def cpu_baseline_sample(args, target_s=15.0):
+    """The oracle as it stands on the host cores: one process per core, each on
+    its own seed (independent replicas, as the GPU ranks), then one process alone."""
+    mcs = int(args.mcs)
+    n1, dt1 = oracle_job3d(SAMPLE_EDGE, mcs, W4.seed)
+    cores = os.cpu_count() or 1
+    ctx = mproc.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(SAMPLE_EDGE, mcs, W4.seed + 1 + i) for i in range(cores)])
     dt = time.perf_counter() - t0
-    return int(np.prod(L)) * mcs, dt
-
-
-SAMPLE_L = (1024, 1024)
-SAMPLE_G = 625  # same sites per grain as 4096^2 / 10^4
-
-
-def cpu_baseline_sample(target_s=12.0):
-    mcs = 60
-    n, dt = oracle_job(SAMPLE_L, SAMPLE_G, mcs, W.seed)
-    return {"value": round(n / dt, 1), "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{SAMPLE_L[0]}x{SAMPLE_L[1]} lattice, {SAMPLE_G} grains (same density), {mcs} MCS, "
-                      f"whole job (voronoi, field, sweep, counts/texture), single thread", "seconds": round(dt, 2)}
+    n = sum(r[0] for r in res)
+    return {"value": round(n / dt, 1), "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+            "single_thread_value": round(n1 / dt1, 1),
+            "sample": f"{SAMPLE_EDGE}^3 lattice of the same grain density ({max(1, round(W4.G * SAMPLE_EDGE**3 / W4.N))} "
+                      f"grains), one refresh period (2 plasticity increments at every material point, Eq. (4) field, "
+                      f"{mcs} MCS), Voronoi and counts included; {cores} independent processes (one per host core) "
+                      f"for `value`, one process alone for `single_thread_value`",
+            "seconds": round(dt, 2), "single_thread_seconds": round(dt1, 2)}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    mcs = 40
+    mcs = int(args.mcs)
     for _ in range(args.warmup):
-        oracle_job((256, 256), 39, 4, W.seed)
+        oracle_job3d(16, 2, W4.seed)
     tot_n, tot_s = 0, 0.0
-    for _ in range(args.steps):
-        n, dt = oracle_job(SAMPLE_L, SAMPLE_G, mcs, W.seed)
+    for k in range(args.steps):
+        n, dt = oracle_job3d(SAMPLE_EDGE, mcs, W4.seed + k)
         tot_n += n
         tot_s += dt
     v = tot_n / tot_s
+    L, N, G = shape3d(args.edge)
     line = {
         "metric": "Potts site-updates/s", "value": round(v, 1), "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_s / args.steps * 1e3, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "impl": "reference",
-        "config": {"workload": W.name, "lattice": list(W.L), "nbr": W.nbr, "grains": W.G, "kT": W.kT,
-                   "mcs_per_step": W.n_mcs, "parallelism": "cpu oracle"},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32 sweep; fp64 plasticity", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"3d-{L[0]}-moore26-g{G}-plain-mcp-hybrid", "lattice": list(L), "nbr": 26,
+                   "grains": G, "kT": W4.kT, "mcs_per_step": mcs, "parallelism": "cpu oracle, one process"},
         "cpu_baseline": {"value": round(v, 1), "unit": "site-updates/s", "kind": "oracle", "cores": 1,
-                         "sample": f"each step: {SAMPLE_L[0]}x{SAMPLE_L[1]}, {SAMPLE_G} grains, {mcs} MCS whole job"},
+                         "sample": f"each step: {SAMPLE_EDGE}^3 lattice of the same grain density, one refresh "
+                                   f"period (2 plasticity increments, Eq. (4) field, {mcs} MCS), own seed"},
         "e2e": {"value": round(v, 1), "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -446,10 +534,6 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # other workloads (one JSON line each; not part of the default run)
 # ---------------------------------------------------------------------------
-def _events(torch):
-    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-
 def run_3d_cp(args):
     """512^3, 26 neighbours, 2e5 grains, MCP refresh every 50 MCS (2 increments of 1e-4), kT 0.7."""
     import torch
@@ -685,14 +769,63 @@ def run_texture(args):
                           "warmup": "one untimed run of 2 increments"}))
 
 
+def run_2d(args):
+    """The 4096^2 Moore line on its own (partly L2-resident; not the HBM figure)."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm
+    build.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"metric": "Potts site-updates/s", **run_2d_secondary(torch, hm)}))
+
+
+def run_texture_seeds(args):
+    """Both 1024^3 hybrids over `--seeds` seeds each: the texture family fractions
+    and the mean max Schmid factor of the two arms compared within two standard
+    errors, and each arm's wall time to 500 MCS (the surrogate trained once)."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm, hybrid
+    build.build()
+    torch.cuda.set_device(0)
+    L, N, G = shape3d(args.edge)
+    prm = hybrid.cp_params_table1(1e-4, 7.0)
+    t0 = time.perf_counter()
+    params, load, loss, _ = hybrid.train_surrogate(torch, prm)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    plain, sur = [], []
+    for k in range(args.seeds):
+        cfg = hybrid.HybridConfig(L=L, G=G, seed=W4.seed + 100 * k, kT=W4.kT, n_mcs=args.mcs)
+        plain.append(hybrid.run_plain(torch, cfg, time_it=False))
+        torch.cuda.empty_cache()
+        sur.append(hybrid.run_surrogate(torch, cfg, params, load, time_it=False))
+        torch.cuda.empty_cache()
+    fp = np.array([r["families"] for r in plain])
+    fs = np.array([r["families"] for r in sur])
+    mp_ = np.array([r["mean_mmax"] for r in plain])
+    ms = np.array([r["mean_mmax"] for r in sur])
+    rows = []
+    for name, a, b in [("none", fp[:, 0], fs[:, 0]), ("100", fp[:, 1], fs[:, 1]), ("110", fp[:, 2], fs[:, 2]),
+                       ("111", fp[:, 3], fs[:, 3]), ("mean_mmax", mp_, ms)]:
+        se = float(np.sqrt(a.var(ddof=1) / len(a) + b.var(ddof=1) / len(b)))
+        d = float(a.mean() - b.mean())
+        rows.append({"quantity": name, "plain_mean": round(float(a.mean()), 6), "surrogate_mean": round(float(b.mean()), 6),
+                     "difference": round(d, 6), "two_se": round(2 * se, 6), "within_2se": bool(abs(d) <= 2 * se + 1e-9)})
+    print(json.dumps({"workload": f"texture-seeds-3d-{L[0]}-g{G}", "seeds_per_arm": args.seeds, "mcs": args.mcs,
+                      "agreement": rows, "all_within_2se": all(r["within_2se"] for r in rows),
+                      "plain_s_mean": round(float(np.mean([r["wall_s"] for r in plain])), 3),
+                      "surrogate_run_s_mean": round(float(np.mean([r["wall_s"] for r in sur])), 3),
+                      "surrogate_train_s": round(train_s, 3),
+                      "time_to_texture_s": {"plain": round(float(np.mean([r["wall_s"] for r in plain])), 3),
+                                            "surrogate": round(train_s + float(np.mean([r["wall_s"] for r in sur])), 3)},
+                      "final_train_loss": loss}))
+
+
 def main():
     args = parse()
-    if args.workload in ("texture2d", "texture3d") and args.impl == "ours":
-        run_texture(args)
-        return
-    if args.workload != "2d" and args.impl == "ours":
-        {"3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
-         "sweep3d": run_sweep3d}[args.workload](args)
+    if args.impl == "ours" and args.workload not in ("3d",):
+        {"2d": run_2d, "3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
+         "sweep3d": run_sweep3d, "texture2d": run_texture, "texture3d": run_texture,
+         "texture-seeds": run_texture_seeds}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
