@@ -6,8 +6,10 @@
 // (colours 0-3, their z-neighbours the odd planes as they were) and then the odd
 // planes (colours 4-7, their z-neighbours the even planes as just updated).  One
 // CTA = one 64 x WY window of one plane with its two z-neighbour windows: q (and,
-// with material points, mp) of the three planes, filled by bulk TMA row copies
-// completing on one mbarrier.  The window keeps a halo of four columns and two
+// with material points, mp) of the three planes, filled by 16-byte asynchronous
+// copies that every thread issues (a few hundred small bulk copies from one warp
+// queue up behind each other in the copy engine; spread over all threads they
+// overlap the draws).  The window keeps a halo of four columns and two
 // rows on each side (the exact region of the four in-plane phases, as in the 2D
 // Moore tiles), so the core is (64 - 8) x (WY - 4).
 //
@@ -23,12 +25,29 @@
 //    both grains among the 26 neighbours with two shared loads per row and run
 //    the integer Metropolis test of Sec. 4.
 // Each phase is then: propose + enqueue, barrier, test + flip, barrier.
+#include <string.h>
+
+#include <cudaTypedefs.h>
+
 #include "sweep.cuh"
 
 namespace hp {
 namespace {
 
 __device__ int g_lean_err;
+
+// Tiled TMA descriptors of the launch's source arrays (3D, Lx x Ly x Lz int32,
+// box 64 x WY x 1); zeroed when a window is never copied by TMA.
+struct alignas(64) LeanMaps {
+    CUtensorMap q_in, q_nb, mp_in, mp_nb;
+    int ok;  // 1: the descriptors are valid
+};
+
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
+}
 
 
 template <int WY, bool HASMP>
@@ -70,7 +89,7 @@ __global__ void k_wait_probe(long long limit, int late) {
 
 template <int WY, int FIELD, bool HASMP>
 __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::MINB)
-    k_lean26(const __grid_constant__ PlaneArgs a) {
+    k_lean26(const __grid_constant__ PlaneArgs a, const __grid_constant__ LeanMaps maps) {
     using Cfg = LeanCfg<WY, HASMP>;
     constexpr int WX = Cfg::WX, PS = Cfg::PS, NA = Cfg::NA, NSUB = Cfg::NSUB, PER = Cfg::PER, kLT = Cfg::kLT;
     constexpr int NW = Cfg::NW;
@@ -99,32 +118,51 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
         return (pl == 1 ? a.mp_in : a.mp_nb) + sxy * zz;
     };
 
-    // ---- window in flight --------------------------------------------------
-    const bool tma = a.Lx % 4 == 0 && WX <= a.Lx && ((uintptr_t)a.q_in & 15u) == 0 && ((uintptr_t)a.q_nb & 15u) == 0 &&
+    // ---- window in flight ----------------------------------------------------
+    // A window inside the lattice arrives as one tiled TMA box per array (64 x WY
+    // of plane z, one request each, completing on an mbarrier that warp 0 polls).
+    // A window that crosses the periodic edge is filled with 16-byte asynchronous
+    // copies issued by every thread (4 ints of one window row each: x0 - 4 and Lx
+    // are multiples of 4, so a chunk never straddles the edge).  Either way the
+    // copies land while the draws below run.
+    const bool vec = a.Lx % 4 == 0 && ((uintptr_t)a.q_in & 15u) == 0 && ((uintptr_t)a.q_nb & 15u) == 0 &&
                      (!HASMP || (((uintptr_t)a.mp_in & 15u) == 0 && ((uintptr_t)a.mp_nb & 15u) == 0));
-    const uint32_t mb = s_addr(mbar);
+    const bool boxed = vec && maps.ok && x0 >= 4 && x0 - 4 + WX <= a.Lx && y0 >= 2 && y0 - 2 + WY <= a.Ly;
     if (tid < 26) {
         const int kk = tid + (tid >= 13);
         off[tid] = (kk / 9 - 1) * PS + ((kk / 3) % 3 - 1) * WX + (kk % 3 - 1);
     }
     if (tid < 4) qn[tid] = 0;
-    if (tma) {
+    const uint32_t mb = s_addr(mbar);
+    if (boxed) {
         if (tid == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
-        if (warp == 0) {
-            if (lane == 0)
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                             "r"((uint32_t)(NA * PS * 4)) : "memory");
-            __syncwarp();
-            for (int i = lane; i < NA * WY; i += 32) {
-                const int arr = i / WY, r = i - arr * WY;
-                copy_row(base + arr * PS + r * WX, src(arr) + (int64_t)a.Lx * gy_of(r), x0 - 4, WX, a.Lx, mb);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                         "r"((uint32_t)(NA * PS * 4)) : "memory");
+            const int xs = x0 - 4, ys = y0 - 2;
+            tma_box(s_addr(base), &maps.q_nb, xs, ys, zlo, mb);
+            tma_box(s_addr(base + PS), &maps.q_in, xs, ys, z, mb);
+            tma_box(s_addr(base + 2 * PS), &maps.q_nb, xs, ys, zhi, mb);
+            if (HASMP) {
+                tma_box(s_addr(base + 3 * PS), &maps.mp_nb, xs, ys, zlo, mb);
+                tma_box(s_addr(base + 4 * PS), &maps.mp_in, xs, ys, z, mb);
+                tma_box(s_addr(base + 5 * PS), &maps.mp_nb, xs, ys, zhi, mb);
             }
         }
+    } else if (vec) {
+        constexpr int CH = WX / 4;  // chunks per window row
+        for (int i = tid; i < NA * WY * CH; i += kLT) {
+            const int arr = i / (WY * CH), rem = i - arr * (WY * CH), r = rem / CH, c = rem - r * CH;
+            const int gx = fast ? wrap1(x0 - 4 + 4 * c, a.Lx) : wrapi(x0 - 4 + 4 * c, a.Lx);
+            const int32_t* g = src(arr) + (int64_t)a.Lx * gy_of(r) + gx;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_addr(base + arr * PS + r * WX + 4 * c)),
+                         "l"(g) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
+    // every thread sees the barrier initialised (and the offsets) before it waits
+    __syncthreads();
 
     // ---- every draw of the launch, while the copies land -------------------
     // site m of phase p for this thread: colour sub-grid column = lane, row
@@ -149,8 +187,11 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
         }
     }
 
-    if (tma) {
+    if (boxed) {
         if (!wait_or_drain(mb, &g_lean_err)) return;
+    } else if (vec) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
     } else {
         for (int i = tid; i < NA * PS; i += kLT) {
             const int arr = i / PS, rem = i - arr * PS, r = rem / WX, c = rem - r * WX;
@@ -252,6 +293,36 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
     }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Descriptor of one int32 lattice array (Lx x Ly x Lz) with a 64 x WY x 1 box;
+// false when it cannot be encoded (the kernel then copies every window with
+// asynchronous 16-byte copies instead).
+bool encode_box(CUtensorMap* m, const void* base, const PlaneArgs& a, int WY) {
+    memset(m, 0, sizeof(*m));
+    PFN_cuTensorMapEncodeTiled_v12000 enc = map_encoder();
+    if (!enc || !base || a.Lx % 4 != 0 || ((uintptr_t)base & 15u) != 0) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)a.Lx, (cuuint64_t)a.Ly, (cuuint64_t)a.Lz};
+    cuuint64_t strides[2] = {(cuuint64_t)a.Lx * 4, (cuuint64_t)a.Lx * (cuuint64_t)a.Ly * 4};
+    cuuint32_t box[3] = {64u, (cuuint32_t)WY, 1u};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3u, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int WY, int FIELD, bool HASMP>
 int launch_lean(const PlaneArgs& a, int planes, cudaStream_t s) {
     using Cfg = LeanCfg<WY, HASMP>;
@@ -263,8 +334,13 @@ int launch_lean(const PlaneArgs& a, int planes, cudaStream_t s) {
         configured = true;
     }
     if (a.tiles == 0 || planes == 0) return HP_OK;
+    LeanMaps maps;
+    memset(&maps, 0, sizeof(maps));
+    bool ok = a.Lx >= 64 && encode_box(&maps.q_in, a.q_in, a, WY) && encode_box(&maps.q_nb, a.q_nb, a, WY);
+    if (ok && HASMP) ok = encode_box(&maps.mp_in, a.mp_in, a, WY) && encode_box(&maps.mp_nb, a.mp_nb, a, WY);
+    maps.ok = ok ? 1 : 0;
     count_launch();
-    k_lean26<WY, FIELD, HASMP><<<dim3((unsigned)a.tiles, (unsigned)planes), Cfg::kLT, smem, s>>>(a);
+    k_lean26<WY, FIELD, HASMP><<<dim3((unsigned)a.tiles, (unsigned)planes), Cfg::kLT, smem, s>>>(a, maps);
     HP_LAUNCH_CHECK("k_lean26");
     return HP_OK;
 }

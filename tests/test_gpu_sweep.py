@@ -156,3 +156,29 @@ def test_sweep_arbitrary_threshold_table(oracle, kind, variant):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(q.cpu().numpy(), ref_q)
     lat.close()
+
+
+@pytest.mark.parametrize("mode", ["none", "grain", "point"])
+@pytest.mark.parametrize("variant", [8, 9, 10, 11])
+def test_lean_3d_interior_and_edge_windows(oracle, mode, variant):
+    """The lean 3D kernel fills windows inside the lattice by tiled TMA boxes and
+    windows that cross the periodic edge by 16-byte asynchronous copies; a
+    lattice with several of each gives the oracle's lattice and material points."""
+    torch, hm = need_gpu()
+    L, Q = (176, 124, 10), 11
+    q0, bgrain, bmp, mp0 = _inputs(L, Q, 77)
+    seed, kT, n = 0x5EED, 0.7, 3
+    thr, D = oracle.threshold_table(kT)
+    if mode == "none":
+        ref_q, _, ref_mp, _ = oracle.sweep(3, L, 26, 256, seed, 2, n, thr, D, q0, None, mp0)
+    elif mode == "grain":
+        ref_q, _, ref_mp, _ = oracle.sweep(3, L, 26, 256, seed, 2, n, thr, D, q0, bgrain[q0], mp0)
+    else:
+        ref_q, _, ref_mp, _ = oracle.sweep(3, L, 26, 256, seed, 2, n, thr, D, q0, bmp[mp0], mp0)
+    fm = {"none": hm.FIELD_NONE, "grain": hm.FIELD_GRAIN, "point": hm.FIELD_POINT}[mode]
+    table = {"none": None, "grain": bgrain, "point": bmp}[mode]
+    q, mp = run_gpu_sweep(torch, hm, 3, L, 26, 256, seed, n, kT, q0, fm, table, mp0, kernel=2, sweep0=2,
+                          variant=variant)
+    np.testing.assert_array_equal(q, ref_q)
+    np.testing.assert_array_equal(mp, ref_mp)
+    assert hm.hp_sweep_status() == 0
