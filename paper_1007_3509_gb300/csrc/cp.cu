@@ -13,7 +13,8 @@
 //   (relative error ~1e-6 for load steps of 1e-4); the chosen system's map is
 //   then solved to convergence by Newton in FP64 and committed;
 //   p_a = exp(-beta (dE_a - min dE)) / Z (Eq. (1)); R = u0 / 2^32 from
-//   Philox(seed; p, t, tag 1); first a with R < sum_{b<=a} p_b (Eq. (2));
+//   Philox(seed; p, t, tag 1); first a with R < sum_{b<=a} p_b (Eq. (2)),
+//   all in FP32 (FP64 is kept for the return map alone);
 //   commit eps_p += x sign P, gamma += x, g = g(gamma + x).
 // After the last increment: sigma = C : (eps_c - eps_p); E_rho = 2 g^2 / G
 // (Eq. (4) with sigma_f = g; the Burgers vector cancels); w = 1/2 sigma : ee;
@@ -136,25 +137,27 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
             dE[al] = -xx * at + 0.5f * xx * xx * k;
             dEmin = fminf(dEmin, dE[al]);
         }
-        double Z = 0.0;
+        float Z = 0.0f;
         float wgt[12];
 #pragma unroll
         for (int al = 0; al < 12; ++al) {
             wgt[al] = (mask >> al & 1) ? expf(-a.beta * (dE[al] - dEmin)) : 0.0f;
-            Z += (double)wgt[al];
+            Z += wgt[al];
         }
         const uint4 u = draw(a.seed, (uint64_t)p, t, kTagMcp, 0);
         // first a with R < sum_{b <= a} w_b / Z, tested as R Z < sum_{b <= a} w_b
-        // (no division per candidate; FP64 sums)
-        const double RZ = (double)u.x * (1.0 / 4294967296.0) * Z;
-        double cum = 0.0;
+        // (no division per candidate; FP32 sums of at most 12 positive terms,
+        // relative error near 1e-7, far inside the 1e-5 band around a decision
+        // where the FP64 oracle and this kernel may legitimately differ)
+        const float RZ = (float)u.x * (1.0f / 4294967296.0f) * Z;
+        float cum = 0.0f;
         int pick = -1, last = -1;
         float tau_pick = 0.0f;
 #pragma unroll
         for (int al = 0; al < 12; ++al) {
             if (!(mask >> al & 1)) continue;
             last = al;
-            cum += (double)wgt[al];
+            cum += wgt[al];
             if (pick < 0 && RZ < cum) { pick = al; tau_pick = tau[al]; }
         }
         if (pick < 0) {
