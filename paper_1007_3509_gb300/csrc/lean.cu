@@ -87,13 +87,14 @@ __global__ void k_wait_probe(long long limit, int late) {
     wait_or_drain(mb, &g_lean_err, limit);
 }
 
+// One window (tile `tile` of plane 2 zidx + a.zpar) of one lattice; maps NULL
+// when no window of this launch is copied by TMA boxes.
 template <int WY, int FIELD, bool HASMP>
-__global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::MINB)
-    k_lean26(const __grid_constant__ PlaneArgs a, const __grid_constant__ LeanMaps maps) {
+__device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* maps, const int tile, const int zidx,
+                                          unsigned char* raw) {
     using Cfg = LeanCfg<WY, HASMP>;
     constexpr int WX = Cfg::WX, PS = Cfg::PS, NA = Cfg::NA, NSUB = Cfg::NSUB, PER = Cfg::PER, kLT = Cfg::kLT;
     constexpr int NW = Cfg::NW;
-    extern __shared__ __align__(16) unsigned char raw[];
     int32_t* base = reinterpret_cast<int32_t*>(raw + ((128u - (s_addr(raw) & 127u)) & 127u));
     int32_t* Q = base + PS;                                       // q of plane z (z-1 at -PS, z+1 at +PS)
     int32_t* MP = base + 4 * PS;                                  // mp of plane z, same layout
@@ -103,9 +104,9 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
     unsigned long long* mbar = reinterpret_cast<unsigned long long*>(qn + 4);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
+    const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
     const int x0 = tx * Cfg::TX, y0 = ty * Cfg::TY;
-    const int z = 2 * (int)blockIdx.y + a.zpar;
+    const int z = 2 * zidx + a.zpar;
     const int zlo = wrapi(z - 1, a.Lz), zhi = wrapi(z + 1, a.Lz);
     const int64_t sxy = (int64_t)a.Lx * a.Ly;
     const bool fast = a.fast != 0;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
     // copies land while the draws below run.
     const bool vec = a.Lx % 4 == 0 && ((uintptr_t)a.q_in & 15u) == 0 && ((uintptr_t)a.q_nb & 15u) == 0 &&
                      (!HASMP || (((uintptr_t)a.mp_in & 15u) == 0 && ((uintptr_t)a.mp_nb & 15u) == 0));
-    const bool boxed = vec && maps.ok && x0 >= 4 && x0 - 4 + WX <= a.Lx && y0 >= 2 && y0 - 2 + WY <= a.Ly;
+    const bool boxed = vec && maps && maps->ok && x0 >= 4 && x0 - 4 + WX <= a.Lx && y0 >= 2 && y0 - 2 + WY <= a.Ly;
     if (tid < 26) {
         const int kk = tid + (tid >= 13);
         off[tid] = (kk / 9 - 1) * PS + ((kk / 3) % 3 - 1) * WX + (kk % 3 - 1);
@@ -141,13 +142,13 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
                          "r"((uint32_t)(NA * PS * 4)) : "memory");
             const int xs = x0 - 4, ys = y0 - 2;
-            tma_box(s_addr(base), &maps.q_nb, xs, ys, zlo, mb);
-            tma_box(s_addr(base + PS), &maps.q_in, xs, ys, z, mb);
-            tma_box(s_addr(base + 2 * PS), &maps.q_nb, xs, ys, zhi, mb);
+            tma_box(s_addr(base), &maps->q_nb, xs, ys, zlo, mb);
+            tma_box(s_addr(base + PS), &maps->q_in, xs, ys, z, mb);
+            tma_box(s_addr(base + 2 * PS), &maps->q_nb, xs, ys, zhi, mb);
             if (HASMP) {
-                tma_box(s_addr(base + 3 * PS), &maps.mp_nb, xs, ys, zlo, mb);
-                tma_box(s_addr(base + 4 * PS), &maps.mp_in, xs, ys, z, mb);
-                tma_box(s_addr(base + 5 * PS), &maps.mp_nb, xs, ys, zhi, mb);
+                tma_box(s_addr(base + 3 * PS), &maps->mp_nb, xs, ys, zlo, mb);
+                tma_box(s_addr(base + 4 * PS), &maps->mp_in, xs, ys, z, mb);
+                tma_box(s_addr(base + 5 * PS), &maps->mp_nb, xs, ys, zhi, mb);
             }
         }
     } else if (vec) {
@@ -293,6 +294,39 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::M
     }
 }
 
+template <int WY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::MINB)
+    k_lean26(const __grid_constant__ PlaneArgs a, const __grid_constant__ LeanMaps maps) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    lean_body<WY, FIELD, HASMP>(a, &maps, (int)blockIdx.x, (int)blockIdx.y, raw);
+}
+
+// Many independent lattices in one launch: block b belongs to the replica r
+// with start[r] <= b < start[r+1]; within it b - start[r] = zidx * tiles + tile.
+// Windows are filled by the asynchronous 16-byte copies.
+template <int WY, int FIELD, bool HASMP>
+__global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, HASMP ? 3 : 4)
+    k_lean26_batch(const PlaneArgs* __restrict__ args, const int64_t* __restrict__ start, int R, uint32_t sweep_add) {
+    extern __shared__ __align__(16) unsigned char raw[];
+    __shared__ PlaneArgs sa;
+    __shared__ int s_tile, s_zidx;
+    if (threadIdx.x == 0) {
+        const int64_t blk = blockIdx.x;
+        int lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= blk) lo = mid; else hi = mid - 1;
+        }
+        sa = args[lo];
+        sa.sweep += sweep_add;
+        const int64_t local = blk - start[lo];
+        s_zidx = (int)(local / sa.tiles);
+        s_tile = (int)(local - (int64_t)s_zidx * sa.tiles);
+    }
+    __syncthreads();
+    lean_body<WY, FIELD, HASMP>(sa, nullptr, s_tile, s_zidx, raw);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool tried = false;
@@ -323,16 +357,30 @@ bool encode_box(CUtensorMap* m, const void* base, const PlaneArgs& a, int WY) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Opt both kernels of an instantiation into their dynamic shared memory, once.
 template <int WY, int FIELD, bool HASMP>
-int launch_lean(const PlaneArgs& a, int planes, cudaStream_t s) {
-    using Cfg = LeanCfg<WY, HASMP>;
-    constexpr size_t smem = Cfg::smem();
+int lean_configure(size_t smem) {
     static bool configured = false;
     if (!configured) {
         HP_CUDA(cudaFuncSetAttribute(k_lean26<WY, FIELD, HASMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
+        HP_CUDA(cudaFuncSetAttribute(k_lean26_batch<WY, FIELD, HASMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
         configured = true;
     }
+    return HP_OK;
+}
+#define HP_CUDA_ONCE_ATTR(WY_, F_, M_, SM_)                   \
+    do {                                                      \
+        const int rc_ = lean_configure<WY_, F_, M_>(SM_);     \
+        if (rc_) return rc_;                                  \
+    } while (0)
+
+template <int WY, int FIELD, bool HASMP>
+int launch_lean(const PlaneArgs& a, int planes, cudaStream_t s) {
+    using Cfg = LeanCfg<WY, HASMP>;
+    constexpr size_t smem = Cfg::smem();
+    HP_CUDA_ONCE_ATTR(WY, FIELD, HASMP, smem);
     if (a.tiles == 0 || planes == 0) return HP_OK;
     LeanMaps maps;
     memset(&maps, 0, sizeof(maps));
@@ -343,6 +391,30 @@ int launch_lean(const PlaneArgs& a, int planes, cudaStream_t s) {
     k_lean26<WY, FIELD, HASMP><<<dim3((unsigned)a.tiles, (unsigned)planes), Cfg::kLT, smem, s>>>(a, maps);
     HP_LAUNCH_CHECK("k_lean26");
     return HP_OK;
+}
+
+template <int WY, int FIELD, bool HASMP>
+int launch_lean_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, int64_t blocks, uint32_t sweep_add,
+                      cudaStream_t s) {
+    using Cfg = LeanCfg<WY, HASMP>;
+    constexpr size_t smem = Cfg::smem();
+    HP_CUDA_ONCE_ATTR(WY, FIELD, HASMP, smem);
+    if (blocks == 0) return HP_OK;  // configure only (outside a graph capture)
+    count_launch();
+    k_lean26_batch<WY, FIELD, HASMP><<<(unsigned)blocks, Cfg::kLT, smem, s>>>(d_args, d_start, R, sweep_add);
+    HP_LAUNCH_CHECK("k_lean26_batch");
+    return HP_OK;
+}
+
+template <int WY>
+int lean_fm_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, int64_t blocks, uint32_t sweep_add, int field,
+                  bool m, cudaStream_t s) {
+    if (field == HP_FIELD_POINT) return launch_lean_batch<WY, 2, true>(d_args, d_start, R, blocks, sweep_add, s);
+    if (field == HP_FIELD_GRAIN)
+        return m ? launch_lean_batch<WY, 1, true>(d_args, d_start, R, blocks, sweep_add, s)
+                 : launch_lean_batch<WY, 1, false>(d_args, d_start, R, blocks, sweep_add, s);
+    return m ? launch_lean_batch<WY, 0, true>(d_args, d_start, R, blocks, sweep_add, s)
+             : launch_lean_batch<WY, 0, false>(d_args, d_start, R, blocks, sweep_add, s);
 }
 
 template <int WY>
@@ -359,6 +431,15 @@ int lean_launch(const PlaneArgs& a, int field, bool hasmp, int planes, int WY, c
     if (WY == 40) return lean_fm<40>(a, field, hasmp, planes, s);
     if (WY == 36) return lean_fm<36>(a, field, hasmp, planes, s);
     if (WY == 32) return lean_fm<32>(a, field, hasmp, planes, s);
+    return set_error(HP_ERR_ARG, "sweep: no lean kernel of this shape");
+}
+
+int lean_launch_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, int64_t blocks, uint32_t sweep_add,
+                      int field, bool hasmp, int WY, cudaStream_t s) {
+    if (WY == 44) return lean_fm_batch<44>(d_args, d_start, R, blocks, sweep_add, field, hasmp, s);
+    if (WY == 40) return lean_fm_batch<40>(d_args, d_start, R, blocks, sweep_add, field, hasmp, s);
+    if (WY == 36) return lean_fm_batch<36>(d_args, d_start, R, blocks, sweep_add, field, hasmp, s);
+    if (WY == 32) return lean_fm_batch<32>(d_args, d_start, R, blocks, sweep_add, field, hasmp, s);
     return set_error(HP_ERR_ARG, "sweep: no lean kernel of this shape");
 }
 

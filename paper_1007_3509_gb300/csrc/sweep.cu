@@ -469,7 +469,7 @@ int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
 // Lean tiles (tile.cu): WX x (TY + 4) row-major windows fed by bulk TMA copies.
 // Lean 3D windows (lean.cu, 26 neighbours): 64 x (TY + 4), every draw made
 // while the window is in flight.  All give identical lattices; the autotuner
-// picks one.  Ensembles take the plane and lean tiles.
+// picks one.  Ensembles take every variant.
 struct Variant {
     int WX, TY;
     bool tile;
@@ -529,8 +529,8 @@ int launch_variant(int nbr, int v, int field, bool m, const PlaneArgs* a, const 
                    int planes, cudaStream_t s) {
     const Variant var = variant_of(nbr, v);
     if (var.lean) {
-        if (!a) return set_error(HP_ERR_ARG, "sweep: lean variants serve single lattices only");
-        return blocks == 0 ? HP_OK : lean_launch(*a, field, m, planes, window_rows(var), s);
+        if (a) return blocks == 0 ? HP_OK : lean_launch(*a, field, m, planes, window_rows(var), s);
+        return lean_launch_batch(b->args, b->start, b->R, blocks, b->sweep_add, field, m, window_rows(var), s);
     }
     if (var.tile) {
         if (a) return blocks == 0 ? HP_OK : tile_launch(*a, field, m, nbr, planes, var.WX, window_rows(var), s);
@@ -567,7 +567,7 @@ bool variant_ok(int nbr, int v, int field, bool m) {
 
 bool variant_batch_ok(int nbr, int v, int field, bool m) {
     const Variant var = variant_of(nbr, v);
-    return variant_ok(nbr, v, field, m) && !var.lean;
+    return variant_ok(nbr, v, field, m);
 }
 
 // Arguments of the fused kernel for one lattice and one launch.

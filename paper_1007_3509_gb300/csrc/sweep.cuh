@@ -181,6 +181,9 @@ int tile_status(int* timed_out);
 // Lean 3D kernel (lean.cu): one launch over the planes of one parity; 64 x WY
 // windows (WY 40 or 44), draws made while the window is in flight.
 int lean_launch(const PlaneArgs& a, int field, bool hasmp, int planes, int WY, cudaStream_t s);
+// The same over many lattices (see tile_launch_batch).
+int lean_launch_batch(const PlaneArgs* d_args, const int64_t* d_start, int R, int64_t blocks, uint32_t sweep_add,
+                      int field, bool hasmp, int WY, cudaStream_t s);
 // Reads and clears the lean kernel's timeout flag (2: a drain ran out too).
 int lean_status(int* timed_out);
 
