@@ -178,12 +178,13 @@ HP_API int hp_set_sweep_kernel(hp_handle* h, int32_t kind);
  * which advances by n_mcs.  On return the state is in the bound buffers.     */
 HP_API int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream);
 
-/* Tile variants of the fused sweep kernel: plane tiles (window width x core
- * height, plain or TMA-fed persistent), warp strips (one warp walks a strip of
- * one plane, rows streamed by bulk TMA copies) and lean tiles (row-major
- * windows filled by bulk TMA copies).  All give identical lattices; ensembles take
- * the plain plane tiles and the lean tiles.  Variants 0-4 (2D) / 0-5 (3D) are plane
- * tiles, 5-8 (2D) / 6-8 (3D) strips, 9-11 (and 12 in 3D) lean tiles.
+/* Tile variants of the fused sweep kernel, all giving identical lattices:
+ * plane tiles (parity-split window, variants 0-2 in 2D, 0-3 in 3D), lean tiles
+ * (row-major windows fed by bulk copies, 3-5 in 2D, 4-7 in 3D) and, for the
+ * 26-neighbour lattice, lean 3D windows (64 x 44, 40, 36, 32: variants 8-11;
+ * every random number drawn while the window is in flight).  Until a variant is
+ * chosen, a handle sweeps with the fastest measured for its kind of lattice:
+ * variant 11 in 3D with material points, 8 in 3D without, 4 in 2D.
  * hp_sweep_variants: how many exist for `nbr`.
  * hp_set_sweep_variant: choose one (HP_ERR_ARG if not built for the handle's
  * field mode).  hp_sweep_autotune: time every variant for n_mcs MCS on a
@@ -314,9 +315,9 @@ HP_API int hp_ensemble_create(hp_handle* const* members, int32_t R, hp_ensemble*
 /* Free the ensemble's graph, capture stream and device argument arrays; the
  * members stay valid and belong to the caller.  Safe with NULL.              */
 HP_API int hp_ensemble_destroy(hp_ensemble* e);
-/* Tile variant used by hp_ensemble_sweep (default 0): plain plane tiles and
- * lean tiles only; HP_ERR_ARG for TMA-fed plane tiles, strips or a variant
- * not built for the members' field mode.                                     */
+/* Tile variant used by hp_ensemble_sweep (default 0); HP_ERR_ARG for a variant
+ * not built for the members' field mode.  Lean 3D windows of an ensemble are
+ * filled by 16-byte asynchronous copies (no tiled TMA descriptors per member). */
 HP_API int hp_ensemble_set_variant(hp_ensemble* e, int32_t v);
 /* Pick the fastest tile variant for the whole ensemble (state restored).      */
 HP_API int hp_ensemble_autotune(hp_ensemble* e, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream);

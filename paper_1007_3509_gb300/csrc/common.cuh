@@ -88,7 +88,7 @@ struct hp_handle {
     int32_t thr_cap = 0;
     uint64_t sweep = 0;
     int sweep_kernel = HP_SWEEP_AUTO;
-    int sweep_variant = 0;      // tile variant of the fused kernel (autotuned)
+    int sweep_variant = -1;     // tile variant of the fused kernel (-1: the lattice's default)
     // owned scratch of hp_measure (allocated on its first call)
     unsigned long long* m_counts = nullptr;  // int64[G]
     int32_t* m_bins = nullptr;               // int32[2G]

@@ -616,6 +616,16 @@ int plane_launch_batch(int nbr, int variant, int field, bool m, const PlaneArgs*
     return launch_variant(nbr, variant, field, m, nullptr, &b, blocks, 1, s);
 }
 
+// Variant a handle sweeps with until one is chosen (hp_set_sweep_variant or the
+// autotuner): the fastest measured on the benchmark lattices -- in 3D the lean
+// 64 x 32 window with material points (four blocks per SM) and the 64 x 44 one
+// without; in 2D the 128 x 60 lean tile.
+int default_variant(const hp_handle* h) {
+    if (h->lat.nbr == 26) return h->mp ? 11 : 8;
+    if (h->lat.nbr == 8 || h->lat.nbr == 4) return 4;
+    return 0;
+}
+
 int sweep_variants(int nbr) { return n_variants(nbr); }
 bool sweep_variant_ok(int nbr, int v, int field, bool m) { return variant_ok(nbr, v, field, m); }
 bool sweep_variant_batch_ok(int nbr, int v, int field, bool m) { return variant_batch_ok(nbr, v, field, m); }
@@ -636,7 +646,7 @@ int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
         return HP_OK;
     }
     const bool m = h->mp != nullptr;
-    const int v = h->sweep_variant;
+    const int v = h->sweep_variant >= 0 ? h->sweep_variant : default_variant(h);
     int32_t *qc = h->q, *mc = h->mp, *qa = h->q_alt, *ma = m ? h->mp_alt : nullptr;
     for (int32_t t = 0; t < n_mcs; ++t) {
         const uint32_t sw = (uint32_t)(h->sweep + t);
