@@ -72,6 +72,8 @@ def _declare(L):
     L.oracle_orientations.argtypes = [i32, u64, C.c_int, P(f32)]
     L.oracle_grain_counts.argtypes = [i64, P(i32), i32, P(i64), P(i32)]
     L.oracle_grain_bins.argtypes = [i32, C.c_int, P(f32), P(i32), P(dbl)]
+    L.oracle_mcp_run_strain.argtypes = [P(CPParams), u64, i64, P(i32), P(f32), u32, P(dbl), P(dbl), P(dbl),
+                                        P(dbl), P(dbl), P(dbl)]
     L.oracle_directional_modulus.argtypes = [P(dbl), P(dbl)]
     L.oracle_directional_modulus.restype = dbl
     L.oracle_max_schmid.argtypes = [P(dbl)]
@@ -331,6 +333,24 @@ def mcp_run(P, seed, grain, quat, t0, n_incr, eps_p, gamma):
     _check(lib().oracle_mcp_run(C.byref(P), C.c_uint64(seed), n, _p(grain, C.c_int32), _p(q, C.c_float),
                                 C.c_uint32(t0), int(n_incr), _p(ep, C.c_double), _p(gm, C.c_double),
                                 _p(sg, C.c_double), _p(nR, C.c_double), _p(nT, C.c_double)), "mcp_run")
+    return ep, gm, sg, nR, nT
+
+
+def mcp_run_strain(P, seed, grain, quat, t, eps_total, eps_p, gamma):
+    """One increment t over all points, point p driven by its own sample-frame
+    total strain eps_total[p] (Voigt xx yy zz yz xz xy, tensor components);
+    returns (eps_p, gamma, sigma, near_R, near_tau)."""
+    grain = np.ascontiguousarray(grain, dtype=np.int32)
+    q = np.ascontiguousarray(quat, dtype=np.float32)
+    n = grain.size
+    et = np.ascontiguousarray(eps_total, dtype=np.float64).reshape(n, 6)
+    ep = np.ascontiguousarray(eps_p, dtype=np.float64).reshape(n, 6).copy()
+    gm = np.ascontiguousarray(gamma, dtype=np.float64).copy()
+    sg = np.empty((n, 6))
+    nR = np.empty(n); nT = np.empty(n)
+    _check(lib().oracle_mcp_run_strain(C.byref(P), C.c_uint64(seed), n, _p(grain, C.c_int32), _p(q, C.c_float),
+                                       C.c_uint32(t), _p(et, C.c_double), _p(ep, C.c_double), _p(gm, C.c_double),
+                                       _p(sg, C.c_double), _p(nR, C.c_double), _p(nT, C.c_double)), "mcp_run_strain")
     return ep, gm, sg, nR, nT
 
 

@@ -580,14 +580,33 @@ static void voigt_from_sym(const double t[3][3], double* v) {
     v[0] = t[0][0]; v[1] = t[1][1]; v[2] = t[2][2]; v[3] = t[1][2]; v[4] = t[0][2]; v[5] = t[0][1];
 }
 
+/* One increment t of one material point whose total strain in the sample
+ * frame is es_v (Voigt xx yy zz yz xz xy, tensor components): the Taylor form
+ * of Eq. (3) below passes t e diag(1, -1/2, -1/2); the elastic-equilibrium
+ * coupling passes the point's own strain from the periodic elastic solve.      */
+int oracle_mcp_increment_strain(const oracle_cp_params* P, uint64_t seed, int64_t p_index, uint32_t t,
+                                const float* quat, const double* es_v, double* eps_p_v, double* gamma,
+                                double* sigma_v, double* near_R, double* near_tau, int32_t* chosen,
+                                int32_t* n_cand);
+
 int oracle_mcp_increment(const oracle_cp_params* P, uint64_t seed, int64_t p_index, uint32_t t,
                          const float* quat, double* eps_p_v, double* gamma, double* sigma_v,
                          double* near_R, double* near_tau, int32_t* chosen, int32_t* n_cand) {
+    const double es_v[6] = {(double)t * P->e_incr, -0.5 * (double)t * P->e_incr, -0.5 * (double)t * P->e_incr,
+                            0.0, 0.0, 0.0};
+    return oracle_mcp_increment_strain(P, seed, p_index, t, quat, es_v, eps_p_v, gamma, sigma_v, near_R, near_tau,
+                                       chosen, n_cand);
+}
+
+int oracle_mcp_increment_strain(const oracle_cp_params* P, uint64_t seed, int64_t p_index, uint32_t t,
+                                const float* quat, const double* es_v, double* eps_p_v, double* gamma,
+                                double* sigma_v, double* near_R, double* near_tau, int32_t* chosen,
+                                int32_t* n_cand) {
     const double Cc[3] = {P->C11, P->C12, P->C44};
     double q[4] = {quat[0], quat[1], quat[2], quat[3]}, R[3][3];
     quat_to_R(q, R);
-    double es[3][3] = {{0}};
-    es[0][0] = (double)t * P->e_incr; es[1][1] = -0.5 * (double)t * P->e_incr; es[2][2] = -0.5 * (double)t * P->e_incr;
+    double es[3][3];
+    sym_from_voigt(es_v, es);
     double ec[3][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
@@ -736,6 +755,22 @@ int oracle_mcp_run(const oracle_cp_params* P, uint64_t seed, int64_t npts, const
         }
         if (near_R) near_R[p] = nr_min;
         if (near_tau) near_tau[p] = nt_min;
+    }
+    return OR_OK;
+}
+
+/* One increment t over P points, point p with its own sample-frame total
+ * strain eps_total[6*p..] (the elastic-equilibrium coupling).                  */
+int oracle_mcp_run_strain(const oracle_cp_params* P, uint64_t seed, int64_t npts, const int32_t* grain,
+                          const float* quat, uint32_t t, const double* eps_total, double* eps_p, double* gamma,
+                          double* sigma, double* near_R, double* near_tau) {
+    for (int64_t p = 0; p < npts; ++p) {
+        double nr, nt;
+        int32_t ch, nc;
+        oracle_mcp_increment_strain(P, seed, p, t, quat + 4 * grain[p], eps_total + 6 * p, eps_p + 6 * p,
+                                    gamma + p, sigma + 6 * p, &nr, &nt, &ch, &nc);
+        if (near_R) near_R[p] = nr;
+        if (near_tau) near_tau[p] = nt;
     }
     return OR_OK;
 }
