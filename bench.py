@@ -216,10 +216,10 @@ class Hybrid3D:
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the 3D sweep
-# kernel (one plane parity of the 1024^3 lattice, the point-field lean window),
-# from an ncu capture of that exact kernel; keyed by tile variant.  None for any
-# other kernel or once the kernel has changed since the capture.
-MEASURED_TRAFFIC_3D = {}
+# kernel (one plane parity, the point-field lean window), from an ncu capture of
+# that exact kernel on the bench lattice (profiles/k_lean26_3d1024_point_field.md);
+# keyed by (edge, tile variant).  None for any other kernel or lattice.
+MEASURED_TRAFFIC_3D = {(1024, 11): 12.950e9 + 4.278e9}
 
 
 def sweep_kernel_name(nbr, variant):
@@ -283,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = peaks()
     variant = job.tuned.get("variant") if job.tuned else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": MEASURED_TRAFFIC_3D.get(variant),
+            "frac": round(achieved / peak, 4), "traffic": MEASURED_TRAFFIC_3D.get((job.L[0], variant)),
             "peak_source": peak_kind, "kernel": sweep_kernel_name(26, variant),
             "bytes_per_site_update": BYTES_3D_POINT, "site_updates_per_launch": job.N // 2,
             "launch_ms": round(launch_s * 1e3, 4),
@@ -700,13 +700,17 @@ def run_surrogate(args):
 
 
 def run_sweep3d(args):
-    """The 3D 512^3 26-neighbour sweep alone (per-point field, material-point index carried)."""
+    """The 3D 26-neighbour sweep alone on an edge^3 lattice (default 512^3, 2e5 grains
+    at that size, the same mean grain volume at others) with a per-point field and
+    the material-point index carried."""
     import torch
     from paper_1007_3509_gb300 import build, hmcpotts as hm
     build.build()
     torch.cuda.set_device(0)
-    L, N = (512, 512, 512), 512 ** 3
-    lat = hm.Lattice(3, L, 26, 256, 1002, 200_000, hm.FIELD_POINT)
+    e = int(args.edge or 512)
+    L, N = (e, e, e), e ** 3
+    G = max(1, round(200_000 * N / 512 ** 3))
+    lat = hm.Lattice(3, L, 26, 256, 1002, G, hm.FIELD_POINT)
     q = torch.empty(N, dtype=torch.int32, device="cuda")
     mp = torch.empty(N, dtype=torch.int32, device="cuda")
     lat.hp_bind(q, mp)
@@ -732,7 +736,8 @@ def run_sweep3d(args):
     rate = N * args.mcs / s
     peak, _ = peaks()
     print(json.dumps({"metric": "Potts site-updates/s", "value": round(rate, 1), "unit": "site-updates/s",
-                      "config": {"workload": "3d-512-moore26-point-field", "variant": int(chosen), "mcs": args.mcs},
+                      "config": {"workload": f"3d-{e}-moore26-g{G}-point-field", "variant": int(chosen),
+                                 "kernel": sweep_kernel_name(26, chosen), "mcs": args.mcs},
                       "roofline": {"bound": "hbm", "bytes_per_site_update": BYTES_3D_POINT,
                                    "achieved": round(rate * BYTES_3D_POINT / 1e9, 1),
                                    "peak": peak, "frac": round(rate * BYTES_3D_POINT / 1e9 / peak, 4)}}))
