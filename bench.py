@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--edge", type=int, default=None,
                    help="3D workloads: lattice edge (default 1024, or 512 for 3d-cp); grains scale with the volume")
     p.add_argument("--workload", choices=["3d", "2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
-                                          "texture3d", "texture-seeds"], default="3d",
+                                          "texture3d", "texture-seeds", "3d-eq"], default="3d",
                    help="3d: 1024^3 plasticity-driven hybrid (default line); 2d: 4096^2 Moore; 3d-cp: 512^3 "
                         "plasticity-driven whole job; ensemble: 256 replicas; surrogate: 1024^3 plain vs surrogate "
                         "time-to-texture; texture-seeds: both arms over 8 seeds each")
@@ -66,7 +66,7 @@ def parse():
     a = p.parse_args()
     if a.mcs is None:
         a.mcs = {"3d": 50, "2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20,
-                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500}[a.workload]
+                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500}[a.workload]
     return a
 
 
@@ -825,12 +825,40 @@ def run_texture_seeds(args):
                       "final_train_loss": loss}))
 
 
+def run_3d_eq(args):
+    """The plasticity-driven hybrid with each increment iterated to periodic elastic
+    equilibrium (Sec. 5) against the Taylor coupling of Eq. (3), same lattice
+    (default 256^3, 32000 grains), 500 MCS, refresh every 50 MCS (2 increments)."""
+    import torch
+    from paper_1007_3509_gb300 import build, hybrid
+    build.build()
+    torch.cuda.set_device(0)
+    e = int(args.edge or 256)
+    L = (e, e, e)
+    G = max(1, round(W4.G * e ** 3 / W4.N))
+    cfg = hybrid.HybridConfig(L=L, G=G, seed=1002, kT=W4.kT, n_mcs=args.mcs)
+    hybrid.run_plain(torch, hybrid.HybridConfig(L=L, G=G, seed=1002, kT=W4.kT, n_mcs=50), coupling="equilibrium")
+    out = {}
+    for coupling in ("taylor", "equilibrium"):
+        r = hybrid.run_plain(torch, cfg, coupling=coupling)
+        out[coupling] = {"wall_s": round(r["wall_s"], 3), "field_s": round(r["field_s"], 3),
+                         "families": [round(x, 5) for x in r["families"]], "mean_mmax": round(r["mean_mmax"], 5),
+                         "alive": r["alive"]}
+        if coupling == "equilibrium":
+            it = r["elastic_iterations"]
+            out[coupling]["elastic_solves"] = len(it)
+            out[coupling]["elastic_iterations_mean"] = round(float(np.mean(it)), 2)
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"3d-{e}-moore26-g{G}-equilibrium-vs-taylor", "mcs": args.mcs,
+                      "refresh": "every 50 MCS, 2 increments of 1e-4", "elastic_tolerance": 1e-5, **out}))
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload not in ("3d",):
         {"2d": run_2d, "3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
          "sweep3d": run_sweep3d, "texture2d": run_texture, "texture3d": run_texture,
-         "texture-seeds": run_texture_seeds}[args.workload](args)
+         "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -369,6 +369,42 @@ HP_API int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream);
 HP_API int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat, uint32_t t0,
                int32_t n_incr, hp_cp_state* st, float* sigma, float* w, float* erho, int32_t* b, void* stream);
 
+/* Periodic elastic equilibrium of the polycrystal (Sec. 5: the plasticity is
+ * coupled to a deformation solver and every load increment is iterated to
+ * quasi-static equilibrium).  One material point per voxel of an n[0] x n[1] x
+ * n[2] grid (linear index x + n0 (y + n1 z), edges powers of two up to 1024).
+ * Solves sigma = C(x) : (eps - eps_p), div sigma = 0, <eps> = E by the
+ * Moulinec-Suquet fixed point with the isotropic reference medium mu0 = (C44 +
+ * (C11 - C12)/2)/2, lambda0 = (C11 + 2 C12)/3 - 2 mu0/3; the strain fluctuation
+ * is zero on the Nyquist planes.  C(x): cubic (prm C11, C12, C44) rotated by
+ * quat[4 grain[x]]; eps_p: crystal-frame plastic strain, device float[6][N]
+ * (the hp_cp_state layout; NULL = none); E: host double[6] sample-frame mean
+ * strain; eps: device float[6][N] sample-frame strain, the initial guess on
+ * entry (or set to E first when start_from_mean) and the solution on return;
+ * sigma (device float[6][N], may be NULL): the sample-frame stress.  Stops
+ * when the largest change of a strain component in one iteration is below
+ * tol max|E| or after max_iter; *iters and *change (may be NULL) report the
+ * iteration count and the last relative change.  FP32; allocates its work
+ * buffer (six complex fields, 48 bytes per voxel) for the call; synchronous.
+ * Voigt order xx yy zz yz xz xy, tensor components throughout.              */
+typedef struct {
+    int32_t n[3];
+    double tol;
+    int32_t max_iter;
+    int32_t start_from_mean;
+} hp_elastic_params;
+HP_API int hp_elastic_solve(const hp_cp_params* prm, const hp_elastic_params* ep, const int32_t* grain,
+                            const float* quat, const float* eps_p, const double E[6], float* eps, float* sigma,
+                            int32_t* iters, double* change, void* stream);
+
+/* One load increment t of every material point with the point's own total
+ * strain (sample frame, device float[6][P], e.g. from hp_elastic_solve) in
+ * place of the Taylor strain of hp_cp_step; otherwise as hp_cp_step with
+ * n_incr = 1 (the draws are keyed by t).                                     */
+HP_API int hp_cp_step_strain(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat,
+                             uint32_t t, const float* eps_total, hp_cp_state* st, float* sigma, float* w, float* erho,
+                             int32_t* b, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned field surrogate: 11 -> 64 -> 64 -> 64 -> 2 perceptron with GELU,    */
 /* BF16 operands and FP32 accumulation on the tensor cores.  It maps a grain's */

@@ -47,6 +47,7 @@ struct CPArgs {
     uint32_t t0;
     int32_t n_incr;
     int64_t P;
+    const float* eps_total;  // sample-frame total strain [6][P] per point, or null (Taylor)
     float* eps_p;
     float* gamma;
     float* g;
@@ -76,6 +77,7 @@ __device__ __forceinline__ double exp_neg(double y) {
     return exp(-y);
 }
 
+template <bool STRAIN>
 __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.P) return;
@@ -93,6 +95,25 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
 #pragma unroll
     for (int v = 0; v < 6; ++v)
         U[v] = R[0][I[v]] * R[0][J[v]] - 0.5f * (R[1][I[v]] * R[1][J[v]] + R[2][I[v]] * R[2][J[v]]);
+    // a point with its own total strain (elastic-equilibrium coupling): the
+    // crystal-frame strain R^T eps R takes the place of t e U
+    float Ut[6];
+    if (STRAIN) {
+        float es[3][3];
+        const float e0 = a.eps_total[p], e1 = a.eps_total[a.P + p], e2 = a.eps_total[2 * a.P + p];
+        const float e3 = a.eps_total[3 * a.P + p], e4 = a.eps_total[4 * a.P + p], e5 = a.eps_total[5 * a.P + p];
+        es[0][0] = e0; es[1][1] = e1; es[2][2] = e2;
+        es[1][2] = es[2][1] = e3; es[0][2] = es[2][0] = e4; es[0][1] = es[1][0] = e5;
+#pragma unroll
+        for (int v = 0; v < 6; ++v) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) acc += R[k][I[v]] * es[k][l] * R[l][J[v]];
+            Ut[v] = acc;
+        }
+    }
     float ep[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v) ep[v] = a.eps_p[(int64_t)v * a.P + p];
@@ -106,7 +127,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         const uint32_t t = a.t0 + (uint32_t)inc;
         const float et = (float)t * a.e;
 #pragma unroll
-        for (int v = 0; v < 6; ++v) ee[v] = et * U[v] - ep[v];
+        for (int v = 0; v < 6; ++v) ee[v] = (STRAIN ? Ut[v] : et * U[v]) - ep[v];
         stress(a, ee, s);
         float tau[12];
         int mask = 0;
@@ -209,7 +230,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         const uint32_t t = a.t0 + (uint32_t)a.n_incr;
         const float et = (float)t * a.e;
 #pragma unroll
-        for (int v = 0; v < 6; ++v) ee[v] = et * U[v] - ep[v];
+        for (int v = 0; v < 6; ++v) ee[v] = (STRAIN ? Ut[v] : et * U[v]) - ep[v];
         stress(a, ee, s);
         if (a.sigma)
 #pragma unroll
@@ -311,10 +332,35 @@ extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t*
     a.beta = (float)prm->beta; a.G = (float)prm->G; a.e = (float)prm->e_incr; a.scale = (float)prm->energy_scale;
     a.w_weight = (float)prm->w_weight;
     a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t0; a.n_incr = n_incr; a.P = st->P;
+    a.eps_total = nullptr;
     a.eps_p = st->eps_p; a.gamma = st->gamma; a.g = st->g;
     a.sigma = sigma; a.w = w; a.erho = erho; a.b = b;
     ::hp::count_launch();
-    k_cp<<<(unsigned)((st->P + kT - 1) / kT), kT, 0, as_stream(stream)>>>(a);
+    k_cp<false><<<(unsigned)((st->P + kT - 1) / kT), kT, 0, as_stream(stream)>>>(a);
+    HP_LAUNCH_CHECK("k_cp");
+    return HP_OK;
+}
+
+extern "C" int hp_cp_step_strain(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat,
+                                 uint32_t t, const float* eps_total, hp_cp_state* st, float* sigma, float* w,
+                                 float* erho, int32_t* b, void* stream) {
+    if (!prm || !st || !grain || !quat || !eps_total || t < 1 || st->P < 1 || !st->eps_p || !st->gamma || !st->g)
+        return set_error(HP_ERR_ARG, "hp_cp_step_strain: bad arguments");
+    if (!(prm->C11 > prm->C12) || !(prm->C44 > 0) || !(prm->tau0 > 0) || !(prm->G > 0))
+        return set_error(HP_ERR_ARG, "hp_cp_step_strain: bad material constants");
+    int rc = upload_tables(prm);
+    if (rc) return rc;
+    CPArgs a;
+    a.C11 = (float)prm->C11; a.C12 = (float)prm->C12; a.C44 = (float)prm->C44;
+    a.tau0 = prm->tau0; a.taus = prm->taus; a.h0 = prm->h0;
+    a.beta = (float)prm->beta; a.G = (float)prm->G; a.e = (float)prm->e_incr; a.scale = (float)prm->energy_scale;
+    a.w_weight = (float)prm->w_weight;
+    a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t - 1; a.n_incr = 1; a.P = st->P;
+    a.eps_total = eps_total;
+    a.eps_p = st->eps_p; a.gamma = st->gamma; a.g = st->g;
+    a.sigma = sigma; a.w = w; a.erho = erho; a.b = b;
+    ::hp::count_launch();
+    k_cp<true><<<(unsigned)((st->P + kT - 1) / kT), kT, 0, as_stream(stream)>>>(a);
     HP_LAUNCH_CHECK("k_cp");
     return HP_OK;
 }

@@ -65,6 +65,10 @@ class hp_sur_train_params(C.Structure):
                 ("log_every", C.c_int32)]
 
 
+class hp_elastic_params(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("tol", C.c_double), ("max_iter", C.c_int32), ("start_from_mean", C.c_int32)]
+
+
 class hp_cp_state(C.Structure):
     _fields_ = [("P", C.c_int64), ("eps_p", C.c_void_p), ("gamma", C.c_void_p), ("g", C.c_void_p)]
 
@@ -115,6 +119,11 @@ _SIGS = {
     "hp_cp_reset": ([C.POINTER(hp_cp_params), C.POINTER(hp_cp_state), C.c_void_p], C.c_int),
     "hp_cp_step": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                     C.POINTER(hp_cp_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_elastic_solve": ([C.POINTER(hp_cp_params), C.POINTER(hp_elastic_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                          C.c_void_p], C.c_int),
+    "hp_cp_step_strain": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
+                           C.POINTER(hp_cp_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_mlp_param_count": ([C.POINTER(C.c_int64)], C.c_int),
     "hp_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "hp_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -367,6 +376,38 @@ def hp_cp_step(prm, seed, grain, quat, t0, n_incr, eps_p, gamma, g, sigma=None, 
                             _dev(quat, 0, 4, wh + " quat"), C.c_uint32(t0), int(n_incr), C.byref(st),
                             _dev(sigma, 6 * P, 4, wh + " sigma"), _dev(w, P, 4, wh + " w"),
                             _dev(erho, P, 4, wh + " erho"), _dev(b, P, 4, wh + " b"), _stream(stream)))
+
+
+def hp_elastic_solve(prm, shape, grain, quat, E, eps, eps_p=None, sigma=None, tol=1e-6, max_iter=200,
+                     start_from_mean=True, stream=None):
+    """Periodic elastic equilibrium on the grid shape = (nx, ny, nz); eps (device
+    float[6 N]) is the initial guess and the solution.  Returns (iterations, last
+    relative change)."""
+    N = int(np.prod(shape))
+    w = "hp_elastic_solve"
+    ep = hp_elastic_params((C.c_int32 * 3)(*[int(v) for v in shape]), float(tol), int(max_iter),
+                           1 if start_from_mean else 0)
+    Ev = (C.c_double * 6)(*[float(v) for v in E])
+    it, ch = C.c_int32(0), C.c_double(0)
+    G = quat.numel() // 4
+    _check(lib().hp_elastic_solve(C.byref(prm), C.byref(ep), _dev(grain, N, 4, w + " grain"),
+                                  _dev(quat, 4 * G, 4, w + " quat"), _dev(eps_p, 6 * N, 4, w + " eps_p"), Ev,
+                                  _dev(eps, 6 * N, 4, w + " eps"), _dev(sigma, 6 * N, 4, w + " sigma"),
+                                  C.byref(it), C.byref(ch), _stream(stream)))
+    return it.value, ch.value
+
+
+def hp_cp_step_strain(prm, seed, grain, quat, t, eps_total, eps_p, gamma, g, sigma=None, w=None, erho=None, b=None,
+                      stream=None):
+    P = int(grain.numel())
+    nm = "hp_cp_step_strain"
+    st = hp_cp_state(P, _dev(eps_p, 6 * P, 4, nm + " eps_p"), _dev(gamma, P, 4, nm + " gamma"),
+                     _dev(g, P, 4, nm + " g"))
+    _check(lib().hp_cp_step_strain(C.byref(prm), C.c_uint64(seed), _dev(grain, P, 4, nm + " grain"),
+                                   _dev(quat, quat.numel(), 4, nm + " quat"), C.c_uint32(t),
+                                   _dev(eps_total, 6 * P, 4, nm + " eps_total"), C.byref(st),
+                                   _dev(sigma, 6 * P, 4, nm + " sigma"), _dev(w, P, 4, nm + " w"),
+                                   _dev(erho, P, 4, nm + " erho"), _dev(b, P, 4, nm + " b"), _stream(stream)))
 
 
 def hp_sweep_status():

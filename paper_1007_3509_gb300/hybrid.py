@@ -49,8 +49,12 @@ def _texture(lat, quat):
     return {"families": list(st.families), "mean_mmax": st.mean_mmax, "hist": hist, "alive": int(st.alive)}
 
 
-def run_plain(torch, cfg: HybridConfig, time_it=True):
-    """Plain hybrid: MCP at every material point at each refresh."""
+def run_plain(torch, cfg: HybridConfig, time_it=True, coupling="taylor", el_tol=1e-5):
+    """Plain hybrid: MCP at every material point at each refresh.  coupling
+    "taylor": every point takes the prescribed strain of Eq. (3); "equilibrium":
+    each increment first solves periodic elastic equilibrium with the current
+    plastic strain (hp_elastic_solve) and every point takes its own strain
+    (hp_cp_step_strain)."""
     N = int(np.prod(cfg.L))
     lat = hm.Lattice(3, cfg.L, 26, 256, cfg.seed, cfg.G, hm.FIELD_POINT)
     q = torch.empty(N, dtype=torch.int32, device="cuda")
@@ -72,11 +76,23 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
     t0 = time.perf_counter()
     t_field = 0.0
     incr = 0
+    eq = coupling == "equilibrium"
+    eps_tot = torch.empty(6 * N, dtype=torch.float32, device="cuda") if eq else None
+    el_iters = []
     for k in range(cfg.n_mcs // cfg.refresh_every):
         if time_it:
             torch.cuda.synchronize()
         f0 = time.perf_counter()
-        hm.hp_cp_step(prm, cfg.seed, grain, quat, incr, cfg.incr_per_refresh, eps, gam, g, b=b)
+        if eq:
+            for j in range(cfg.incr_per_refresh):
+                t = incr + j + 1
+                E = (t * cfg.e_incr, -0.5 * t * cfg.e_incr, -0.5 * t * cfg.e_incr, 0.0, 0.0, 0.0)
+                it, _ = hm.hp_elastic_solve(prm, cfg.L, grain, quat, E, eps_tot, eps_p=eps, tol=el_tol,
+                                            start_from_mean=(t == 1))
+                el_iters.append(it)
+                hm.hp_cp_step_strain(prm, cfg.seed, grain, quat, t, eps_tot, eps, gam, g, b=b)
+        else:
+            hm.hp_cp_step(prm, cfg.seed, grain, quat, incr, cfg.incr_per_refresh, eps, gam, g, b=b)
         if time_it:
             torch.cuda.synchronize()
         t_field += time.perf_counter() - f0
@@ -86,7 +102,10 @@ def run_plain(torch, cfg: HybridConfig, time_it=True):
     wall = time.perf_counter() - t0
     tex = _texture(lat, quat)
     lat.close()
-    return {"wall_s": wall, "field_s": t_field, **tex}
+    out = {"wall_s": wall, "field_s": t_field, **tex}
+    if eq:
+        out["elastic_iterations"] = el_iters
+    return out
 
 
 def train_surrogate(torch, prm, n_orient=65536, K=128, n_incr=20, steps=60000, lr=2e-3, seed=3000, log_every=0,
