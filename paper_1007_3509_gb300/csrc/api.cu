@@ -122,6 +122,7 @@ extern "C" int hp_bind(hp_handle* h, int32_t* q, int32_t* mp) {
 // Upload (is_host != 0: from pageable or pinned host memory) or take from
 // device memory the lattice state q (and mp) of a bound handle.
 extern "C" int hp_set_spins(hp_handle* h, const int32_t* q, const int32_t* mp, int32_t is_host, void* stream) {
+    hp::Range r_("hp_set_spins");
     if (!h || !q) return set_error(HP_ERR_ARG, "hp_set_spins: null handle or q");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_set_spins: no lattice bound");
     if (mp && !h->mp) return set_error(HP_ERR_STATE, "hp_set_spins: no material-point buffer bound");
@@ -134,6 +135,7 @@ extern "C" int hp_set_spins(hp_handle* h, const int32_t* q, const int32_t* mp, i
 }
 
 extern "C" int hp_get_spins(const hp_handle* h, int32_t* q, int32_t* mp, int32_t is_host, void* stream) {
+    hp::Range r_("hp_get_spins");
     if (!h || !q) return set_error(HP_ERR_ARG, "hp_get_spins: null handle or q");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_get_spins: no lattice bound");
     if (mp && !h->mp) return set_error(HP_ERR_STATE, "hp_get_spins: no material-point buffer bound");
@@ -146,6 +148,7 @@ extern "C" int hp_get_spins(const hp_handle* h, int32_t* q, int32_t* mp, int32_t
 }
 
 extern "C" int hp_init_voronoi(hp_handle* h, int32_t orient_kind, float* orient, int64_t* seed_pos, void* stream) {
+    hp::Range r_("hp_init_voronoi");
     if (!h) return set_error(HP_ERR_ARG, "hp_init_voronoi: null handle");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_init_voronoi: no lattice bound");
     if (orient && (orient_kind < HP_ORIENT_ANGLE || orient_kind > HP_ORIENT_ZROT))
@@ -210,6 +213,7 @@ extern "C" int hp_set_sweep_kernel(hp_handle* h, int32_t kind) {
 }
 
 extern "C" int hp_sweep(hp_handle* h, int32_t n_mcs, void* stream) {
+    hp::Range r_("hp_sweep");
     if (!h || n_mcs < 0) return set_error(HP_ERR_ARG, "hp_sweep: bad arguments");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_sweep: no lattice bound");
     if (!h->thr) return set_error(HP_ERR_STATE, "hp_sweep: no threshold table");

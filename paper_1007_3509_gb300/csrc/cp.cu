@@ -320,6 +320,7 @@ extern "C" int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* strea
 extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat,
                           uint32_t t0, int32_t n_incr, hp_cp_state* st, float* sigma, float* w, float* erho,
                           int32_t* b, void* stream) {
+    hp::Range r_("hp_cp_step");
     if (!prm || !st || !grain || !quat || n_incr < 0 || st->P < 1 || !st->eps_p || !st->gamma || !st->g)
         return set_error(HP_ERR_ARG, "hp_cp_step: bad arguments");
     if (!(prm->C11 > prm->C12) || !(prm->C44 > 0) || !(prm->tau0 > 0) || !(prm->G > 0))
@@ -344,6 +345,7 @@ extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t*
 extern "C" int hp_cp_step_strain(const hp_cp_params* prm, uint64_t seed, const int32_t* grain, const float* quat,
                                  uint32_t t, const float* eps_total, hp_cp_state* st, float* sigma, float* w,
                                  float* erho, int32_t* b, void* stream) {
+    hp::Range r_("hp_cp_step_strain");
     if (!prm || !st || !grain || !quat || !eps_total || t < 1 || st->P < 1 || !st->eps_p || !st->gamma || !st->g)
         return set_error(HP_ERR_ARG, "hp_cp_step_strain: bad arguments");
     if (!(prm->C11 > prm->C12) || !(prm->C44 > 0) || !(prm->tau0 > 0) || !(prm->G > 0))

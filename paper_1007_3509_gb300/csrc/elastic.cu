@@ -294,6 +294,7 @@ using namespace hp;
 extern "C" int hp_elastic_solve(const hp_cp_params* prm, const hp_elastic_params* ep, const int32_t* grain,
                                 const float* quat, const float* eps_p, const double E[6], float* eps, float* sigma,
                                 int32_t* iters, double* change_out, void* stream) {
+    hp::Range r_("hp_elastic_solve");
     if (!prm || !ep || !grain || !quat || !E || !eps) return set_error(HP_ERR_ARG, "hp_elastic_solve: bad arguments");
     for (int d = 0; d < 3; ++d)
         if (ep->n[d] < 1 || ep->n[d] > 1024 || log2_exact(ep->n[d]) < 0)

@@ -241,6 +241,7 @@ extern "C" int hp_grain_field(int32_t G, const float* quat, double C11, double C
 }
 
 extern "C" int hp_grain_counts(hp_handle* h, int64_t* counts, int32_t* alive, void* stream) {
+    hp::Range r_("hp_grain_counts");
     if (!h || !counts) return set_error(HP_ERR_ARG, "hp_grain_counts: bad arguments");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_grain_counts: no lattice bound");
     cudaStream_t s = as_stream(stream);
@@ -291,6 +292,7 @@ enum { kSlotHist = 0, kSlotField = 90, kSlotAlive = 91, kSlotBad = 92, kSlots = 
 
 extern "C" int hp_measure(hp_handle* h, int32_t orient_kind, const float* orient, int32_t accumulate,
                           hp_stats* st, int64_t* hist, int32_t n_bins, void* stream) {
+    hp::Range r_("hp_measure");
     if (!h || !st) return set_error(HP_ERR_ARG, "hp_measure: null handle or stats");
     if (!h->q) return set_error(HP_ERR_STATE, "hp_measure: no lattice bound");
     if (orient && (orient_kind < HP_ORIENT_ANGLE || orient_kind > HP_ORIENT_ZROT))

@@ -649,6 +649,7 @@ int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
     const int v = h->sweep_variant >= 0 ? h->sweep_variant : default_variant(h);
     int32_t *qc = h->q, *mc = h->mp, *qa = h->q_alt, *ma = m ? h->mp_alt : nullptr;
     for (int32_t t = 0; t < n_mcs; ++t) {
+        Range r_("mcs");
         const uint32_t sw = (uint32_t)(h->sweep + t);
         int planes = 1, rc;
         if (nbr == 26) {
@@ -684,6 +685,7 @@ int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
 using namespace hp;
 
 extern "C" int hp_sweep_autotune(hp_handle* h, int32_t n_mcs, float* ms_out, int32_t* chosen, void* stream) {
+    hp::Range r_("hp_sweep_autotune");
     if (!h || n_mcs < 1) return set_error(HP_ERR_ARG, "hp_sweep_autotune: bad arguments");
     if (!h->q || !h->thr) return set_error(HP_ERR_STATE, "hp_sweep_autotune: bind buffers and thresholds first");
     cudaStream_t s = as_stream(stream);
@@ -882,6 +884,7 @@ extern "C" int hp_ensemble_set_variant(hp_ensemble* e, int32_t v) {
 }
 
 extern "C" int hp_ensemble_sweep(hp_ensemble* e, int32_t n_mcs, void* stream) {
+    hp::Range r_("hp_ensemble_sweep");
     if (!e || n_mcs < 0) return set_error(HP_ERR_ARG, "hp_ensemble_sweep: bad arguments");
     if (n_mcs == 0) return HP_OK;
     cudaStream_t s = as_stream(stream);
