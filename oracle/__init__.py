@@ -65,6 +65,9 @@ def _declare(L):
                                P(i32), P(i32), P(i32), P(i64)]
     L.oracle_sweep_phase_slab.argtypes = [C.c_int, P(i64), C.c_int, i32, u64, u32, C.c_int, P(u32), i32, i64, i64,
                                           P(i32), P(i32), P(i32), P(i64)]
+    L.oracle_sweep_aniso.argtypes = [C.c_int, P(i64), C.c_int, u64, u32, i32, P(u32), i32, P(i32), i32, i32, i32,
+                                     P(i32), P(u32), P(i32), P(i32), P(i32), P(i64)]
+    L.oracle_read_shockley.argtypes = [dbl, dbl, i32, i32, i32, P(i32), P(u32)]
     L.oracle_voronoi_seeds.argtypes = [C.c_int, P(i64), i32, u64, P(i64)]
     L.oracle_voronoi_site.argtypes = [C.c_int, P(i64), i32, P(i64), i64]
     L.oracle_voronoi_site.restype = i32
@@ -147,6 +150,34 @@ def sweep(dim, L, nbr, J_fix, seed, sweep0, n_mcs, thr, D, q, b=None, mp=None):
                               int(n_mcs), _p(thr, C.c_uint32), int(D), _p(q, C.c_int32), _p(b, C.c_int32),
                               _p(mp, C.c_int32), C.byref(flips)), "sweep")
     return q, b, mp, flips.value
+
+
+def sweep_aniso(dim, L, nbr, seed, sweep0, n_mcs, thr, D, q, ang, period, bin_w, Jtab, mtab=None, b=None, mp=None):
+    """Sweep with misorientation-dependent pair energy and mobility (Eq. (7) with
+    J_{q_i,q_n}; see the C source).  Returns (q, b, mp, flips)."""
+    Lq = _L3(L)
+    q = np.ascontiguousarray(q, dtype=np.int32).copy()
+    b = None if b is None else np.ascontiguousarray(b, dtype=np.int32).copy()
+    mp = None if mp is None else np.ascontiguousarray(mp, dtype=np.int32).copy()
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    ang = np.ascontiguousarray(ang, dtype=np.int32)
+    Jtab = np.ascontiguousarray(Jtab, dtype=np.int32)
+    mtab = None if mtab is None else np.ascontiguousarray(mtab, dtype=np.uint32)
+    fl = np.zeros(1, dtype=np.int64)
+    _check(lib().oracle_sweep_aniso(dim, _p(Lq, C.c_int64), nbr, C.c_uint64(seed), C.c_uint32(sweep0), n_mcs,
+                                    _p(thr, C.c_uint32), D, _p(ang, C.c_int32), int(period), int(bin_w),
+                                    int(Jtab.size), _p(Jtab, C.c_int32), _p(mtab, C.c_uint32), _p(q, C.c_int32),
+                                    _p(b, C.c_int32), _p(mp, C.c_int32), _p(fl, C.c_int64)), "sweep_aniso")
+    return q, b, mp, int(fl[0])
+
+
+def read_shockley(J_max, theta_max, bin_w, nbins, unit_per_degree, mobility=False):
+    """Read-Shockley energy table (int32, 256 = 1 J) and optionally the mobility table (uint32)."""
+    J = np.empty(nbins, dtype=np.int32)
+    m = np.empty(nbins, dtype=np.uint32) if mobility else None
+    _check(lib().oracle_read_shockley(float(J_max), float(theta_max), int(bin_w), int(nbins), int(unit_per_degree),
+                                      _p(J, C.c_int32), _p(m, C.c_uint32)), "read_shockley")
+    return J, m
 
 
 def sweep_phase_slab(dim, L, nbr, J_fix, seed, sweep, colour, thr, D, s0, ns, q, b=None, mp=None):

@@ -236,6 +236,111 @@ int oracle_sweep(int dim, const int64_t* L, int nbr, int32_t J_fix, uint64_t see
 }
 
 /* ------------------------------------------------------------------------ */
+/* Misorientation-dependent interaction energy and mobility (the pair energy  */
+/* J_{q_i,q_n} of Eq. (7); the arbitrary-misorientation extension of Sec. 6). */
+/* Grain g has an integer orientation angle ang[g] in [0, period) (e.g.       */
+/* millidegrees of a rotation about z, period 90000 for a cubic crystal).     */
+/* The misorientation of grains a, b is min(d, period - d) with               */
+/* d = |ang[a] - ang[b]|; its bin is mis / bin_w (clamped to nbins - 1).      */
+/* J(a, b) = Jtab[bin] (256 = 1 J), mob(a, b) = mtab[bin] (uint32, all ones   */
+/* = 1; NULL = every boundary equally mobile).                                */
+/* Site energy in state s: sum over neighbours n with q_n != s of J(s, q_n).  */
+/* Trial as in oracle_sweep; d = E(q_j) - E(q_i) + (b_j - b_i); with          */
+/* m = mob(q_i, q_j) and t = thr[d] (all ones for d < 0):                     */
+/*   eff = t when m is all ones, m when t is all ones, else floor(t m / 2^32) */
+/*   accept iff d <= D and (eff is all ones or u1 < eff).                    */
+/* A constant Jtab = J_fix without mobility gives oracle_sweep exactly.      */
+/* ------------------------------------------------------------------------ */
+static int32_t mis_bin(const int32_t* ang, int32_t a, int32_t b, int32_t period, int32_t bin_w, int32_t nbins) {
+    int64_t d = (int64_t)ang[a] - (int64_t)ang[b];
+    if (d < 0) d = -d;
+    d %= period;
+    if (period - d < d) d = period - d;
+    int64_t k = d / bin_w;
+    return (int32_t)(k < nbins ? k : nbins - 1);
+}
+
+int oracle_sweep_aniso(int dim, const int64_t* L, int nbr, uint64_t seed, uint32_t sweep0, int32_t n_mcs,
+                       const uint32_t* thr, int32_t D, const int32_t* ang, int32_t period, int32_t bin_w,
+                       int32_t nbins, const int32_t* Jtab, const uint32_t* mtab, int32_t* q, int32_t* b,
+                       int32_t* mp, int64_t* n_flips) {
+    off3 o[26];
+    const int M = neighbourhood(dim, nbr, o);
+    const int C = n_colours(dim, nbr);
+    if (!M || !C || !q || !thr || D < 0 || n_mcs < 0 || !ang || !Jtab || period < 1 || bin_w < 1 || nbins < 1)
+        return OR_ERR_ARG;
+    const int64_t Lx = L[0], Ly = L[1], Lz = dim == 3 ? L[2] : 1;
+    if (Lx < 2 || Ly < 2 || Lz < 1 || (Lx & 1) || (Ly & 1) || (dim == 3 && (Lz & 1))) return OR_ERR_ARG;
+    int64_t flips = 0;
+    for (int32_t t = 0; t < n_mcs; ++t) {
+        const uint32_t sweep = sweep0 + (uint32_t)t;
+        for (int c = 0; c < C; ++c)
+            for (int64_t z = 0; z < Lz; ++z)
+                for (int64_t y = 0; y < Ly; ++y)
+                    for (int64_t x = 0; x < Lx; ++x) {
+                        if (colour_of(dim, nbr, x, y, z) != c) continue;
+                        const int64_t i = x + Lx * (y + Ly * z);
+                        int64_t nb[26];
+                        for (int k = 0; k < M; ++k)
+                            nb[k] = wrap(x + o[k].dx, Lx) + Lx * (wrap(y + o[k].dy, Ly) + Ly * wrap(z + o[k].dz, Lz));
+                        uint32_t u[4];
+                        draw(seed, (uint64_t)i, sweep, TAG_SWEEP, (uint32_t)c, u);
+                        const int k = (int)(((uint64_t)u[0] * (uint64_t)M) >> 32);
+                        const int64_t j = nb[k];
+                        const int32_t qi = q[i], qj = q[j];
+                        if (qj == qi) continue;
+                        int32_t e_old = 0, e_new = 0;
+                        for (int n = 0; n < M; ++n) {
+                            const int32_t qn = q[nb[n]];
+                            if (qn != qi) e_old += Jtab[mis_bin(ang, qi, qn, period, bin_w, nbins)];
+                            if (qn != qj) e_new += Jtab[mis_bin(ang, qj, qn, period, bin_w, nbins)];
+                        }
+                        const int32_t d = e_new - e_old + (b ? (b[j] - b[i]) : 0);
+                        int accept = 0;
+                        if (d <= D) {
+                            const uint32_t tt = d < 0 ? 0xFFFFFFFFu : thr[d];
+                            const uint32_t m = mtab ? mtab[mis_bin(ang, qi, qj, period, bin_w, nbins)] : 0xFFFFFFFFu;
+                            uint32_t eff;
+                            if (m == 0xFFFFFFFFu) eff = tt;
+                            else if (tt == 0xFFFFFFFFu) eff = m;
+                            else eff = (uint32_t)(((uint64_t)tt * (uint64_t)m) >> 32);
+                            accept = eff == 0xFFFFFFFFu || u[1] < eff;
+                        }
+                        if (accept) {
+                            q[i] = qj;
+                            if (b) b[i] = b[j];
+                            if (mp) mp[i] = mp[j];
+                            ++flips;
+                        }
+                    }
+    }
+    if (n_flips) *n_flips = flips;
+    return OR_OK;
+}
+
+/* Read-Shockley boundary energy per misorientation bin (bin centres, in     */
+/* degrees: (k + 1/2) bin_w / unit_per_degree): J(th) = J_max (th/th_m)      */
+/* (1 - ln(th/th_m)) below th_m, J_max above, rounded half-even to 256 = 1 J  */
+/* units; optional mobility m(th) = 1 - exp(-5 (th/th_m)^4) as a uint32       */
+/* fraction (all ones = 1).                                                    */
+int oracle_read_shockley(double J_max, double th_m, int32_t bin_w, int32_t nbins, int32_t unit_per_degree,
+                         int32_t* Jtab, uint32_t* mtab) {
+    if (!(J_max >= 0.0) || !(th_m > 0.0) || bin_w < 1 || nbins < 1 || unit_per_degree < 1 || !Jtab) return OR_ERR_ARG;
+    for (int32_t k = 0; k < nbins; ++k) {
+        const double th = ((double)k + 0.5) * (double)bin_w / (double)unit_per_degree;
+        const double r = th / th_m;
+        const double e = r < 1.0 ? J_max * r * (1.0 - log(r)) : J_max;
+        Jtab[k] = (int32_t)nearbyint(256.0 * e);
+        if (mtab) {
+            const double m = 1.0 - exp(-5.0 * r * r * r * r);
+            const double f = floor(ldexp(m, 32));
+            mtab[k] = f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Initial polycrystal: Voronoi tessellation of G seeds.                     */
 /* Seed placement in rounds: in round a every still-unplaced seed g draws    */
 /* site floor(u0 * N / 2^32) from Philox(seed; g, a, TAG_VORONOI<<24 | 0)    */
