@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--edge", type=int, default=None,
                    help="3D workloads: lattice edge (default 1024, or 512 for 3d-cp); grains scale with the volume")
     p.add_argument("--workload", choices=["3d", "2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
-                                          "texture3d", "texture-seeds", "3d-eq"], default="3d",
+                                          "texture3d", "texture-seeds", "3d-eq", "aniso"], default="3d",
                    help="3d: 1024^3 plasticity-driven hybrid (default line); 2d: 4096^2 Moore; 3d-cp: 512^3 "
                         "plasticity-driven whole job; ensemble: 256 replicas; surrogate: 1024^3 plain vs surrogate "
                         "time-to-texture; texture-seeds: both arms over 8 seeds each")
@@ -66,7 +66,7 @@ def parse():
     a = p.parse_args()
     if a.mcs is None:
         a.mcs = {"3d": 50, "2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20,
-                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500}[a.workload]
+                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500, "aniso": 200}[a.workload]
     return a
 
 
@@ -853,12 +853,51 @@ def run_3d_eq(args):
                       "refresh": "every 50 MCS, 2 increments of 1e-4", "elastic_tolerance": 1e-5, **out}))
 
 
+def run_aniso(args):
+    """Misorientation-dependent pair energy (Read-Shockley, theta_m = 15 degrees) and
+    mobility on the 2D Moore lattice of grains rotated about z (1024^2, 625 grains:
+    the 4096^2 workload's grain density), kT 0.6: site-updates/s of the per-colour
+    kernel with the tables against the same kernel and the fused kernel without."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm
+    build.build()
+    torch.cuda.set_device(0)
+    L, G, N = (1024, 1024), 625, 1024 * 1024
+    out = {}
+    for name in ("pair_energy_and_mobility", "constant_J_per_colour", "constant_J_fused"):
+        lat = hm.Lattice(2, L, 8, 256, 1001, G, hm.FIELD_NONE)
+        q = torch.empty(N, dtype=torch.int32, device="cuda")
+        lat.hp_bind(q)
+        ang = torch.empty(G, device="cuda")
+        lat.hp_init_voronoi(hm.ORIENT_ANGLE, ang)
+        lat.hp_set_threshold_table(*hm.hp_build_threshold_table(0.6))
+        if name == "pair_energy_and_mobility":
+            units = torch.empty(G, dtype=torch.int32, device="cuda")
+            hm.hp_angle_units(G, hm.ORIENT_ANGLE, ang, 1000, 90000, units)
+            J, m = hm.hp_build_read_shockley(1.0, 15.0, 250, 181, 1000, mobility=True)
+            lat.hp_set_anisotropy(units, 90000, 250, J, m)
+        if name == "constant_J_per_colour":
+            lat.hp_set_sweep_kernel(hm.SWEEP_PHASE)
+        lat.hp_sweep(5)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record()
+        lat.hp_sweep(args.mcs)
+        e1.record()
+        torch.cuda.synchronize()
+        st, _ = lat.hp_measure()
+        out[name] = {"site_updates_per_s": round(N * args.mcs / (e0.elapsed_time(e1) / 1e3), 1),
+                     "alive_after": int(st.alive)}
+        lat.close()
+    print(json.dumps({"workload": "aniso-2d-1024-moore8-g625-read-shockley", "mcs": args.mcs, "kT": 0.6, **out}))
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload not in ("3d",):
         {"2d": run_2d, "3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
          "sweep3d": run_sweep3d, "texture2d": run_texture, "texture3d": run_texture,
-         "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq}[args.workload](args)
+         "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq, "aniso": run_aniso}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -154,6 +154,64 @@ HP_API int hp_orientations(int32_t G, uint64_t seed, int32_t orient_kind, float*
  * Host-only bookkeeping: the table is read by the next sweep.                */
 HP_API int hp_set_field(hp_handle* h, const int32_t* table, int64_t n);
 
+/* Misorientation-dependent interaction energy and mobility (the pair energy
+ * J_{q_i,q_n} of Eq. (7); the arbitrary-misorientation extension the paper
+ * names in Sec. 6).  angle: device int32[G] (borrowed), each grain's
+ * orientation as an integer angle in [0, period) (e.g. millidegrees of a
+ * rotation about z, period 90000 for a cubic crystal).  The misorientation of
+ * grains a and b is min(d, period - d), d = |angle_a - angle_b|; its bin is
+ * misorientation / bin, clamped to nbins - 1 (the bins must cover [0,
+ * period/2]).  J: host int32[nbins] energies per bin in [0, 2^20] (256 = 1 J);
+ * mobility: host uint32[nbins] relative mobilities (0xFFFFFFFF = 1) or NULL.
+ * A site's energy in state s is the sum over neighbours n with q_n != s of
+ * J[bin(s, q_n)]; d = E(q_j) - E(q_i) + (b_j - b_i); the threshold of the
+ * trial is scaled by the mobility m of the (q_i, q_j) boundary: eff = thr[d]
+ * (0xFFFFFFFF for d < 0) if m is 0xFFFFFFFF, m if thr[d] is, else
+ * floor(thr[d] m / 2^32); accept iff d <= D and (eff == 0xFFFFFFFF or u1 < eff).
+ * With tables set, hp_sweep runs the per-colour kernel; angle = J = NULL
+ * clears them (back to the constant J_fix).  Copies the tables; synchronises
+ * `stream`.                                                                  */
+HP_API int hp_set_anisotropy(hp_handle* h, const int32_t* angle, int32_t period, int32_t bin, int32_t nbins,
+                             const int32_t* J, const uint32_t* mobility, void* stream);
+
+/* Grain angles in the integer units of hp_set_anisotropy: out[g] =
+ * floor(theta_g [degrees] * unit_per_degree) mod period, theta_g the angle of
+ * HP_ORIENT_ANGLE (device float[G]) or the rotation angle 2 atan2(z, w) of
+ * HP_ORIENT_ZROT (device float[4G]); out device int32[G].                    */
+HP_API int hp_angle_units(int32_t G, int32_t orient_kind, const float* orient, int32_t unit_per_degree,
+                          int32_t period, int32_t* out, void* stream);
+
+/* Read-Shockley tables, host FP64: bin k has the misorientation
+ * theta = (k + 1/2) bin / unit_per_degree degrees, x = theta / theta_max;
+ * J_out[k] = round-half-even(256 J_max x (1 - ln x)) for x < 1, 256 J_max
+ * beyond; mob_out (may be NULL) = floor(2^32 (1 - exp(-5 x^4))), saturated at
+ * 0xFFFFFFFF (low-angle boundaries slow).                                    */
+HP_API int hp_build_read_shockley(double J_max, double theta_max, int32_t bin, int32_t nbins, int32_t unit_per_degree,
+                                  int32_t* J_out, uint32_t* mob_out);
+
+/* Parametric links between the sharp-interface and Monte Carlo models, Eq. (8)
+ * (Sec. 3): from the physical boundary stiffness gamma_s [J/m^2] and mobility
+ * m_s [m^4/(J s)], the length of one lattice unit l0 [m], and the Monte Carlo
+ * counterparts gamma_mc (stiffness in units of J per lattice spacing) and m_mc
+ * (mobility in lattice units per MCS) at the run's temperature, with lattice
+ * spacing Delta, interaction energy J and time step tau_mc (1 MCS = tau_mc):
+ *   E0 = gamma_s Delta^2 J l0^2 / gamma_mc
+ *   t0 = Delta^4 m_mc l0^4 / (J tau_mc E0 m_s),  seconds per MCS = tau_mc t0
+ *   b (MC units) = b_per_bs * b_s  with  b_per_bs = Delta^3 l0^3 / (2 E0)
+ * so a physical bulk energy density b_s [J/m^3] becomes the field of Eq. (7)
+ * and each MCS a physical time (the paper's Sec. 5 runs take 1 MCS = 10 min). */
+typedef struct {
+    double gamma_s, m_s, l0;     /* physical stiffness, mobility, lattice unit   */
+    double gamma_mc, m_mc;       /* Monte Carlo stiffness and mobility           */
+    double Delta, J, tau_mc;     /* lattice spacing, interaction energy, MC step */
+} hp_si_in;
+typedef struct {
+    double E0, t0;               /* characteristic energy [J] and time [s]       */
+    double seconds_per_mcs;      /* physical time of one MCS                     */
+    double b_per_bs;             /* MC bulk energy per unit physical b_s [J/m^3] */
+} hp_si_out;
+HP_API int hp_si_links(const hp_si_in* in, hp_si_out* out);
+
 /* Metropolis threshold table, host FP64 (Sec. 4, acceptance
  * min(1, exp(-dE/kT))): out[0] = 0xFFFFFFFF (dE = 0 accepted) or 0 when
  * zero_rule = 1; out[d] = min(floor(2^32 exp(-d/(256 kT))), 0xFFFFFFFE) for

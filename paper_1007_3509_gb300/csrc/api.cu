@@ -100,6 +100,8 @@ extern "C" int hp_destroy(hp_handle* h) {
     cudaFree(h->q_alt);
     cudaFree(h->mp_alt);
     cudaFree(h->thr);
+    cudaFree(h->an_J);
+    cudaFree(h->an_mob);
     cudaFree(h->m_counts);
     cudaFree(h->m_bins);
     cudaFree(h->m_small);
@@ -248,4 +250,36 @@ extern "C" int hp_debug_wait_timeout(int32_t unit, int64_t limit_cycles, int32_t
     if (unit == 0) return lean_wait_probe((long long)limit_cycles, late, as_stream(stream));
     if (unit == 1) return mlp_wait_probe((long long)limit_cycles, late, as_stream(stream));
     return set_error(HP_ERR_ARG, "hp_debug_wait_timeout: unit must be 0 (sweep) or 1 (surrogate)");
+}
+
+extern "C" int hp_build_read_shockley(double J_max, double theta_max, int32_t bin, int32_t nbins,
+                                      int32_t unit_per_degree, int32_t* J_out, uint32_t* mob_out) {
+    if (!(J_max >= 0.0) || J_max > 4096.0 || !(theta_max > 0.0) || bin < 1 || nbins < 1 || unit_per_degree < 1 ||
+        !J_out)
+        return set_error(HP_ERR_ARG, "hp_build_read_shockley: bad arguments");
+    for (int32_t k = 0; k < nbins; ++k) {
+        const double x = ((double)k + 0.5) * (double)bin / (double)unit_per_degree / theta_max;
+        const double e = x < 1.0 ? J_max * x * (1.0 - log(x)) : J_max;
+        J_out[k] = (int32_t)nearbyint(256.0 * e);
+        if (mob_out) {
+            const double f = floor(ldexp(1.0 - exp(-5.0 * x * x * x * x), 32));
+            mob_out[k] = f >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)f;
+        }
+    }
+    return HP_OK;
+}
+
+extern "C" int hp_si_links(const hp_si_in* in, hp_si_out* out) {
+    if (!in || !out || !(in->gamma_s > 0) || !(in->m_s > 0) || !(in->l0 > 0) || !(in->gamma_mc > 0) ||
+        !(in->m_mc > 0) || !(in->Delta > 0) || !(in->J > 0) || !(in->tau_mc > 0))
+        return set_error(HP_ERR_ARG, "hp_si_links: every quantity must be positive");
+    // Eq. (8): gamma_s = gamma E0 / (Delta^2 J l0^2)  ->  E0
+    //          m_s = Delta^4 m l0^4 / (J tau E0 t0)    ->  t0
+    //          b_s = 2 b E0 / (Delta^3 l0^3)           ->  b per unit b_s
+    const double D = in->Delta, l0 = in->l0;
+    out->E0 = in->gamma_s * D * D * in->J * l0 * l0 / in->gamma_mc;
+    out->t0 = D * D * D * D * in->m_mc * l0 * l0 * l0 * l0 / (in->J * in->tau_mc * out->E0 * in->m_s);
+    out->seconds_per_mcs = in->tau_mc * out->t0;
+    out->b_per_bs = D * D * D * l0 * l0 * l0 / (2.0 * out->E0);
+    return HP_OK;
 }

@@ -99,6 +99,11 @@ struct hp_handle {
     uint64_t sweep = 0;
     int sweep_kernel = HP_SWEEP_AUTO;
     int sweep_variant = -1;     // tile variant of the fused kernel (-1: the lattice's default)
+    // misorientation-dependent pair energy and mobility (hp_set_anisotropy)
+    const int32_t* an_ang = nullptr;  // borrowed grain angles
+    int32_t* an_J = nullptr;          // owned device tables
+    uint32_t* an_mob = nullptr;
+    int32_t an_period = 0, an_bin = 0, an_nbins = 0;
     // owned scratch of hp_measure (allocated on its first call)
     unsigned long long* m_counts = nullptr;  // int64[G]
     int32_t* m_bins = nullptr;               // int32[2G]

@@ -203,6 +203,18 @@ __global__ void __launch_bounds__(kT) k_field_sum_point(const int32_t* __restric
     block_add(v, sum);
 }
 
+// angle [rad] of HP_ORIENT_ANGLE (or the rotation angle of HP_ORIENT_ZROT) to
+// integer units: floor(degrees * unit_per_degree) mod period
+__global__ void k_angle_units(int32_t G, int32_t kind, const float* orient, int32_t unit, int32_t period, int32_t* out) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const double pi = 3.14159265358979323846;
+    const double t = kind == HP_ORIENT_ANGLE ? (double)orient[g]
+                                             : 2.0 * atan2((double)orient[4 * g + 3], (double)orient[4 * g]);
+    int64_t v = (int64_t)floor(t * (180.0 / pi) * (double)unit) % period;
+    out[g] = (int32_t)(v < 0 ? v + period : v);
+}
+
 }  // namespace
 }  // namespace hp
 
@@ -365,5 +377,16 @@ extern "C" int hp_measure(hp_handle* h, int32_t orient_kind, const float* orient
         for (int b = 0; b < nb; ++b) tot += hist[b];
         st->hist_total = tot;
     }
+    return HP_OK;
+}
+
+extern "C" int hp_angle_units(int32_t G, int32_t orient_kind, const float* orient, int32_t unit_per_degree,
+                              int32_t period, int32_t* out, void* stream) {
+    if (G < 1 || !orient || !out || unit_per_degree < 1 || period < 2 ||
+        (orient_kind != HP_ORIENT_ANGLE && orient_kind != HP_ORIENT_ZROT))
+        return set_error(HP_ERR_ARG, "hp_angle_units: bad arguments");
+    ::hp::count_launch();
+    k_angle_units<<<(G + kT - 1) / kT, kT, 0, as_stream(stream)>>>(G, orient_kind, orient, unit_per_degree, period, out);
+    HP_LAUNCH_CHECK("k_angle_units");
     return HP_OK;
 }

@@ -41,13 +41,36 @@ struct PhaseArgs {
     int colour;
     int Lx, Ly, Lz;
     int64_t n_colour_sites;
+    // misorientation-dependent pair energy and mobility (ANI kernels only)
+    const int32_t* ang;   // grain angles (borrowed, G entries)
+    const int32_t* jtab;  // energy per misorientation bin (256 = 1 J)
+    const uint32_t* mob;  // relative mobility per bin (all ones = 1), or null
+    int32_t period, bin_w, nbins, G;
 };
+
+// Misorientation bin of grains a and b: |ang_a - ang_b| folded by the angle's
+// symmetry period, divided by the bin width, clamped to the last bin (grain ids
+// clamped into the table: they come from caller buffers).
+__device__ __forceinline__ int mis_bin(const PhaseArgs& a, int32_t qa, int32_t qb) {
+    const uint32_t ua = (uint32_t)qa < (uint32_t)a.G ? (uint32_t)qa : (uint32_t)(a.G - 1);
+    const uint32_t ub = (uint32_t)qb < (uint32_t)a.G ? (uint32_t)qb : (uint32_t)(a.G - 1);
+    int64_t d = (int64_t)__ldg(a.ang + ua) - (int64_t)__ldg(a.ang + ub);
+    d = (d < 0 ? -d : d) % a.period;
+    if (a.period - d < d) d = a.period - d;
+    const int64_t k = d / a.bin_w;
+    return (int)(k < a.nbins ? k : a.nbins - 1);
+}
 
 // ---------------------------------------------------------------------------
 // One colour phase, one thread per site of that colour, in place.
 // FIELD: 0 none, 1 grain (table[q]), 2 point (table[mp]).
 // ---------------------------------------------------------------------------
-template <int DIM, int NBR, int FIELD, bool HASMP>
+// ANI: the energy of a site in state s is the sum over neighbours n with
+// q_n != s of jtab[bin(s, q_n)], and the Metropolis threshold is scaled by the
+// mobility of the (q_i, q_j) boundary: eff = thr[d] (all ones for d < 0) when
+// the mobility m is all ones, m when thr is all ones, else floor(thr m / 2^32);
+// accept iff d <= D and (eff is all ones or u1 < eff).
+template <int DIM, int NBR, int FIELD, bool HASMP, bool ANI>
 __global__ void __launch_bounds__(kThreads) k_phase(PhaseArgs a) {
     using G = Geo<DIM, NBR>;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,8 +128,26 @@ __global__ void __launch_bounds__(kThreads) k_phase(PhaseArgs a) {
     if (HASMP) mpj = a.mp[j];
     if (FIELD == 1) db = tab(a.table, a.table_n, qj) - tab(a.table, a.table_n, qi);
     if (FIELD == 2) db = tab(a.table, a.table_n, mpj) - tab(a.table, a.table_n, a.mp[i]);
-    const int32_t d = a.J * (same_old - same_new) + db;
-    if (metropolis(d, a.D, a.thr, u.y)) {
+    if (!ANI) {
+        const int32_t d = a.J * (same_old - same_new) + db;
+        if (metropolis(d, a.D, a.thr, u.y)) {
+            a.q[i] = qj;
+            if (HASMP) a.mp[i] = mpj;
+        }
+        return;
+    }
+    int32_t e_old = 0, e_new = 0;
+#pragma unroll
+    for (int k = 0; k < G::M; ++k) {
+        if (nv[k] != qi) e_old += __ldg(a.jtab + mis_bin(a, qi, nv[k]));
+        if (nv[k] != qj) e_new += __ldg(a.jtab + mis_bin(a, qj, nv[k]));
+    }
+    const int32_t d = e_new - e_old + db;
+    if (d > a.D) return;
+    const uint32_t th = d < 0 ? 0xFFFFFFFFu : __ldg(a.thr + d);
+    const uint32_t m = a.mob ? __ldg(a.mob + mis_bin(a, qi, qj)) : 0xFFFFFFFFu;
+    const uint32_t eff = m == 0xFFFFFFFFu ? th : (th == 0xFFFFFFFFu ? m : __umulhi(th, m));
+    if (eff == 0xFFFFFFFFu || u.y < eff) {
         a.q[i] = qj;
         if (HASMP) a.mp[i] = mpj;
     }
@@ -419,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, kPlaneMinBlocks) k_plane_batch(Batch
     plane_body<NBR, WX, TY, FIELD, HASMP>(sa, s_tile, s_zidx, smem);
 }
 
-template <int DIM, int NBR, int FIELD, bool HASMP>
+template <int DIM, int NBR, int FIELD, bool HASMP, bool ANI>
 int launch_phase(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     PhaseArgs a;
     a.q = h->q;
@@ -436,24 +477,39 @@ int launch_phase(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     a.Ly = (int)h->lat.L[1];
     a.Lz = (int)h->lat.L[2];
     a.n_colour_sites = h->lat.N / Geo<DIM, NBR>::C;
+    a.ang = h->an_ang;
+    a.jtab = h->an_J;
+    a.mob = h->an_mob;
+    a.period = h->an_period;
+    a.bin_w = h->an_bin;
+    a.nbins = h->an_nbins;
+    a.G = h->desc.n_grains;
     const int64_t blocks = (a.n_colour_sites + kThreads - 1) / kThreads;
     ::hp::count_launch();
-    k_phase<DIM, NBR, FIELD, HASMP><<<(unsigned)blocks, kThreads, 0, s>>>(a);
+    k_phase<DIM, NBR, FIELD, HASMP, ANI><<<(unsigned)blocks, kThreads, 0, s>>>(a);
     HP_LAUNCH_CHECK("k_phase");
     return HP_OK;
 }
 
-template <int DIM, int NBR>
-int phase_dispatch(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
+template <int DIM, int NBR, bool ANI>
+int phase_dispatch_a(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
     const bool m = h->mp != nullptr;
     switch (h->desc.field_mode) {
         case HP_FIELD_NONE:
-            return m ? launch_phase<DIM, NBR, 0, true>(h, sweep, colour, s) : launch_phase<DIM, NBR, 0, false>(h, sweep, colour, s);
+            return m ? launch_phase<DIM, NBR, 0, true, ANI>(h, sweep, colour, s)
+                     : launch_phase<DIM, NBR, 0, false, ANI>(h, sweep, colour, s);
         case HP_FIELD_GRAIN:
-            return m ? launch_phase<DIM, NBR, 1, true>(h, sweep, colour, s) : launch_phase<DIM, NBR, 1, false>(h, sweep, colour, s);
+            return m ? launch_phase<DIM, NBR, 1, true, ANI>(h, sweep, colour, s)
+                     : launch_phase<DIM, NBR, 1, false, ANI>(h, sweep, colour, s);
         default:
-            return launch_phase<DIM, NBR, 2, true>(h, sweep, colour, s);
+            return launch_phase<DIM, NBR, 2, true, ANI>(h, sweep, colour, s);
     }
+}
+
+template <int DIM, int NBR>
+int phase_dispatch(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
+    return h->an_J ? phase_dispatch_a<DIM, NBR, true>(h, sweep, colour, s)
+                   : phase_dispatch_a<DIM, NBR, false>(h, sweep, colour, s);
 }
 
 int run_phase_kernel(hp_handle* h, uint32_t sweep, int colour, cudaStream_t s) {
@@ -621,9 +677,11 @@ int plane_launch_batch(int nbr, int variant, int field, bool m, const PlaneArgs*
 // 64 x 32 window with material points (four blocks per SM) and the 64 x 44 one
 // without; in 2D the 128 x 60 lean tile.
 int default_variant(const hp_handle* h) {
-    if (h->lat.nbr == 26) return h->mp ? 11 : 8;
-    if (h->lat.nbr == 8 || h->lat.nbr == 4) return 4;
-    return 0;
+    int v = 0;
+    if (h->lat.nbr == 26) v = h->mp ? 11 : 8;
+    else if (h->lat.nbr == 8 || h->lat.nbr == 4) v = 4;
+    // variant 0 is built for every field mode; the others for the production ones
+    return variant_ok(h->lat.nbr, v, h->desc.field_mode, h->mp != nullptr) ? v : 0;
 }
 
 int sweep_variants(int nbr) { return n_variants(nbr); }
@@ -634,7 +692,7 @@ bool sweep_variant_batch_ok(int nbr, int v, int field, bool m) { return variant_
 
 int sweep_run(hp_handle* h, int32_t n_mcs, cudaStream_t s) {
     const int nbr = h->lat.nbr;
-    const bool fused_ok = nbr != 6;
+    const bool fused_ok = nbr != 6 && !h->an_J;  // the pair-energy tables run on the per-colour kernel
     const bool fused = fused_ok && h->sweep_kernel != HP_SWEEP_PHASE;
     if (!fused) {
         for (int32_t t = 0; t < n_mcs; ++t)
@@ -972,4 +1030,32 @@ extern "C" int hp_ensemble_autotune(hp_ensemble* e, int32_t n_mcs, float* ms_out
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == HP_OK) rc = cuda_error(cudaGetLastError(), "hp_ensemble_autotune");
     if (chosen) *chosen = e->variant;
     return rc;
+}
+
+extern "C" int hp_set_anisotropy(hp_handle* h, const int32_t* angle, int32_t period, int32_t bin, int32_t nbins,
+                                 const int32_t* J, const uint32_t* mobility, void* stream) {
+    if (!h) return set_error(HP_ERR_ARG, "hp_set_anisotropy: null handle");
+    cudaFree(h->an_J);
+    cudaFree(h->an_mob);
+    h->an_J = nullptr;
+    h->an_mob = nullptr;
+    h->an_ang = nullptr;
+    if (!angle && !J) return HP_OK;  // back to the isotropic J_fix
+    if (!angle || !J || period < 2 || bin < 1 || nbins < 1 || (int64_t)nbins * bin < period / 2)
+        return set_error(HP_ERR_ARG, "hp_set_anisotropy: bad arguments (the bins must cover [0, period/2])");
+    for (int32_t k = 0; k < nbins; ++k)
+        if (J[k] < 0 || J[k] > (1 << 20)) return set_error(HP_ERR_ARG, "hp_set_anisotropy: J out of [0, 2^20]");
+    cudaStream_t s = as_stream(stream);
+    HP_CUDA(cudaMalloc((void**)&h->an_J, sizeof(int32_t) * (size_t)nbins));
+    HP_CUDA(cudaMemcpyAsync(h->an_J, J, sizeof(int32_t) * (size_t)nbins, cudaMemcpyHostToDevice, s));
+    if (mobility) {
+        HP_CUDA(cudaMalloc((void**)&h->an_mob, sizeof(uint32_t) * (size_t)nbins));
+        HP_CUDA(cudaMemcpyAsync(h->an_mob, mobility, sizeof(uint32_t) * (size_t)nbins, cudaMemcpyHostToDevice, s));
+    }
+    HP_CUDA(cudaStreamSynchronize(s));  // the host tables may be released after return
+    h->an_ang = angle;
+    h->an_period = period;
+    h->an_bin = bin;
+    h->an_nbins = nbins;
+    return HP_OK;
 }

@@ -69,6 +69,15 @@ class hp_elastic_params(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("tol", C.c_double), ("max_iter", C.c_int32), ("start_from_mean", C.c_int32)]
 
 
+class hp_si_in(C.Structure):
+    _fields_ = [("gamma_s", C.c_double), ("m_s", C.c_double), ("l0", C.c_double), ("gamma_mc", C.c_double),
+                ("m_mc", C.c_double), ("Delta", C.c_double), ("J", C.c_double), ("tau_mc", C.c_double)]
+
+
+class hp_si_out(C.Structure):
+    _fields_ = [("E0", C.c_double), ("t0", C.c_double), ("seconds_per_mcs", C.c_double), ("b_per_bs", C.c_double)]
+
+
 class hp_cp_state(C.Structure):
     _fields_ = [("P", C.c_int64), ("eps_p", C.c_void_p), ("gamma", C.c_void_p), ("g", C.c_void_p)]
 
@@ -124,6 +133,12 @@ _SIGS = {
                           C.c_void_p], C.c_int),
     "hp_cp_step_strain": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
                            C.POINTER(hp_cp_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_set_anisotropy": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                           C.c_void_p], C.c_int),
+    "hp_build_read_shockley": ([C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p],
+                               C.c_int),
+    "hp_si_links": ([C.POINTER(hp_si_in), C.POINTER(hp_si_out)], C.c_int),
+    "hp_angle_units": ([C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "hp_mlp_param_count": ([C.POINTER(C.c_int64)], C.c_int),
     "hp_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "hp_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -410,6 +425,29 @@ def hp_cp_step_strain(prm, seed, grain, quat, t, eps_total, eps_p, gamma, g, sig
                                    _dev(erho, P, 4, nm + " erho"), _dev(b, P, 4, nm + " b"), _stream(stream)))
 
 
+def hp_build_read_shockley(J_max, theta_max, bin_w, nbins, unit_per_degree, mobility=False):
+    """Host Read-Shockley tables: (int32 J[nbins] in 256 = 1 J units, uint32 mobility or None)."""
+    J = np.zeros(nbins, dtype=np.int32)
+    m = np.zeros(nbins, dtype=np.uint32) if mobility else None
+    _check(lib().hp_build_read_shockley(float(J_max), float(theta_max), int(bin_w), int(nbins), int(unit_per_degree),
+                                        J.ctypes.data, None if m is None else m.ctypes.data))
+    return J, m
+
+
+def hp_angle_units(G, kind, orient, unit_per_degree, period, out, stream=None):
+    w = "hp_angle_units"
+    _check(lib().hp_angle_units(int(G), int(kind), _dev(orient, _orient_len(kind, G), 4, w + " orient"),
+                                int(unit_per_degree), int(period), _dev(out, G, 4, w + " out"), _stream(stream)))
+
+
+def hp_si_links(gamma_s, m_s, l0, gamma_mc, m_mc, Delta=1.0, J=1.0, tau_mc=1.0):
+    """Eq. (8) links: returns dict(E0, t0, seconds_per_mcs, b_per_bs)."""
+    i = hp_si_in(gamma_s, m_s, l0, gamma_mc, m_mc, Delta, J, tau_mc)
+    o = hp_si_out()
+    _check(lib().hp_si_links(C.byref(i), C.byref(o)))
+    return {"E0": o.E0, "t0": o.t0, "seconds_per_mcs": o.seconds_per_mcs, "b_per_bs": o.b_per_bs}
+
+
 def hp_sweep_status():
     v = C.c_int32(0)
     _check(lib().hp_sweep_status(C.byref(v)))
@@ -577,6 +615,19 @@ class Lattice:
         _check(lib().hp_measure(self._h, kind, o, 0 if acc is None else 1, C.byref(st),
                                 hist.ctypes.data if nb else None, int(hist.size), _stream(stream)))
         return st, hist
+
+    def hp_set_anisotropy(self, angle, period, bin_w, J, mobility=None, stream=None):
+        """Misorientation-dependent pair energy and mobility (angle: CUDA int32[G] or None to clear)."""
+        if angle is None:
+            _check(lib().hp_set_anisotropy(self._h, None, 0, 0, 0, None, None, _stream(stream)))
+            self._aniso = None
+            return
+        J = np.ascontiguousarray(J, dtype=np.int32)
+        m = None if mobility is None else np.ascontiguousarray(mobility, dtype=np.uint32)
+        _check(lib().hp_set_anisotropy(self._h, _dev(angle, self.n_grains, 4, "hp_set_anisotropy angle"), int(period),
+                                       int(bin_w), int(J.size), J.ctypes.data, None if m is None else m.ctypes.data,
+                                       _stream(stream)))
+        self._aniso = angle
 
     def hp_grain_counts(self, counts, alive=None, stream=None):
         _check(lib().hp_grain_counts(self._h, _dev(counts, self.n_grains, 8, "hp_grain_counts counts"),

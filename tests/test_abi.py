@@ -103,3 +103,29 @@ def test_sur_train_argument_errors(hm):
     tp = hm.hp_sur_train_params(10, 0, 1, 1e-3, 0.02, 0.9, 0.999, 1e-8, 5)  # a log without a host array
     assert hm.lib().hp_sur_train(dummy, dummy, dummy, dummy, dummy, 100, C.byref(tp), 0, None, None, None) == \
         hm.HP_ERR_ARG
+
+
+def test_read_shockley_table_matches_oracle(hm, oracle):
+    for args in [(1.0, 15.0, 250, 181, 1000), (2.5, 10.0, 1000, 46, 1000), (0.7, 20.0, 100, 451, 1000)]:
+        J, m = hm.hp_build_read_shockley(*args, mobility=True)
+        rJ, rm = oracle.read_shockley(*args, mobility=True)
+        np.testing.assert_array_equal(J, rJ)
+        np.testing.assert_array_equal(m, rm)
+
+
+def test_si_links_invert_eq8(hm):
+    """The three links of Eq. (8) hold with the returned E0, t0 and b conversion;
+    choosing the physical mobility that makes one MCS last 10 minutes (Sec. 5)
+    gives back 600 s."""
+    gamma_s, m_s, l0, gamma_mc, m_mc, Delta, J, tau = 0.9, 3e-14, 2e-7, 0.7, 0.45, 1.0, 1.0, 1.0
+    r = hm.hp_si_links(gamma_s, m_s, l0, gamma_mc, m_mc, Delta, J, tau)
+    E0, t0 = r["E0"], r["t0"]
+    assert abs(gamma_mc * E0 / (Delta ** 2 * J * l0 ** 2) - gamma_s) <= 1e-12 * gamma_s
+    assert abs(Delta ** 4 * m_mc * l0 ** 4 / (J * tau * E0 * t0) - m_s) <= 1e-12 * m_s
+    b_s = 5e5  # J/m^3
+    b = r["b_per_bs"] * b_s
+    assert abs(2 * b * E0 / (Delta ** 3 * l0 ** 3) - b_s) <= 1e-12 * b_s
+    m10 = Delta ** 4 * m_mc * l0 ** 4 / (J * tau * E0 * 600.0)
+    assert abs(hm.hp_si_links(gamma_s, m10, l0, gamma_mc, m_mc, Delta, J, tau)["seconds_per_mcs"] - 600.0) < 1e-9
+    with pytest.raises(hm.HPError):
+        hm.hp_si_links(0.0, m_s, l0, gamma_mc, m_mc)
