@@ -13,17 +13,23 @@ eps (the increment is the same for every system, as in the Taylor load):
 
   trial stress s_tr = C : (eps - eps_p), resolved shear tau_a = P_a : s_tr,
   signs s_a = sign(tau_a), active set A = {a : |tau_a| - g(gamma) > 0};
-  on A solve  |tau_a| - sum_b A_ab x_b - g(gamma + sum_b x_b) = 0,
+  on A solve  s_a tau_a - sum_b A_ab x_b - g(gamma + sum_b x_b) = 0,
   A_ab = s_a s_b P_a : C : P_b, by Newton steps x <- x - J^+ r with
   J = -(A + g'(gamma + sum x) 1 1^T) and J^+ its pseudo-inverse (numpy pinv:
   the SVD, singular values below 1e-10 of the largest dropped) -- the FCC
   constraints are linearly dependent, hence ill-conditioned;
-  then drop every system with x_a < 0 and solve again; then add every inactive
-  system whose resolved shear exceeds g and solve again; repeat until neither
-  happens; commit eps_p += sum_a x_a s_a P_a, gamma += sum_a x_a.
+  while a slip comes out below -1e-6 tol, drop the system of the most negative
+  slip and solve again; then, while an inactive system's resolved shear exceeds
+  g by more than 10 tol, add the most over-stressed one, with s_a the sign of
+  its current resolved shear (a large increment can reverse it from the
+  trial's), and solve again; at most 50 passes; commit
+  eps_p += sum_a x_a s_a P_a, gamma += sum_a x_a.  Ties go to the lowest
+  system index (the order of FCC_N / FCC_M below).
 
 The paper gives neither the active-set strategy nor the SVD cut-off; the two
-choices above are this build's reading.
+choices above are a reading.  One change at a time matters: dropping every
+negative slip and adding every over-stressed system at once cycles between two
+sets on increments far beyond the yield strain.
 """
 from __future__ import annotations
 
@@ -72,7 +78,7 @@ def _solve(active, sgn, tau_tr, K, p, gamma, tol):
     A = sgn[idx, None] * sgn[None, idx] * K[np.ix_(idx, idx)]
     for _ in range(100):
         gam = gamma + x.sum()
-        r = np.abs(tau_tr[idx]) - A @ x - voce(p, gam)
+        r = sgn[idx] * tau_tr[idx] - A @ x - voce(p, gam)
         if np.abs(r).max() < tol:
             break
         J = -(A + voce_slope(p, gam) * np.ones((idx.size, idx.size)))
@@ -96,7 +102,7 @@ def step(p, C, eps, eps_p, gamma, tol=None):
     for _ in range(50):
         idx, x = _solve(active, sgn, tau, K, p, gamma, tol)
         if (x < -tol * 1e-6).any():
-            active[idx[x < 0]] = False
+            active[idx[np.argmin(x)]] = False
             if not active.any():
                 return eps_p, gamma, s_tr, np.zeros(0, int), np.zeros(0)
             continue
@@ -104,9 +110,11 @@ def step(p, C, eps, eps_p, gamma, tol=None):
         s = np.einsum("ijkl,kl->ij", C, eps - eps_p - dep)
         t = np.einsum("aij,ij->a", P, s)
         g = voce(p, gamma + x.sum())
-        grow = (~active) & (np.abs(t) - g > tol * 10)
-        if grow.any():
-            active |= grow
+        over = np.where(active, -np.inf, np.abs(t) - g)
+        if over.max() > tol * 10:
+            a = int(np.argmax(over))
+            sgn[a] = 1.0 if t[a] >= 0 else -1.0  # slips along its current resolved shear
+            active[a] = True
             continue
         return eps_p + dep, gamma + x.sum(), s, idx, x
     raise RuntimeError("active set did not settle")

@@ -170,7 +170,7 @@ def test_monte_carlo_plasticity_follows_the_deterministic_curve(oracle, seed):
         s_mcp.append((Rf @ S @ Rf.T)[0, 0])
     rel = (np.array(s_mcp) - s_svd) / s_svd
     assert (nact > 0).mean() > 0.5 and nact.max() >= 3
-    assert np.abs(rel[nact <= 1]).max() <= 1e-6
+    assert np.abs(rel[np.maximum.accumulate(nact) <= 1]).max() <= 1e-6  # before any multiple slip
     multi = nact >= 2
     assert 0 <= rel[multi].mean() <= 0.025, rel[multi].mean()
     first = int(np.argmax(multi))
@@ -186,3 +186,28 @@ def svdcp_rot(q):
     return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_large_increments_settle_consistently():
+    """One-shot strains far beyond yield (about 20 yield strains, random
+    directions): the active set settles, every active system sits on the yield
+    surface with non-negative slip, no system lies outside it, and the plastic
+    strain is the slips along the final resolved-shear signs."""
+    from oracle import svdcp
+    p = _p()
+    C = svdcp.stiffness(p["C11"], p["C12"], p["C44"])
+    P = svdcp.schmid()
+    rng = np.random.default_rng(5)
+    for i in range(60):
+        R, _ = _rot(100 + i)
+        e = rng.normal(size=6) * 1.2e-3
+        E = np.array([[e[0], e[5], e[4]], [e[5], e[1], e[3]], [e[4], e[3], e[2]]])
+        Ec = R.T @ E @ R
+        ep, gam, s, idx, x = svdcp.step(p, C, Ec, np.zeros((3, 3)), 0.0)
+        g = svdcp.voce(p, gam)
+        tau = np.einsum("aij,ij->a", P, s)
+        assert np.all(np.abs(tau) <= g * (1 + 1e-9))
+        assert np.all(np.abs(np.abs(tau[idx]) - g) <= 1e-9 * g)
+        assert np.all(x >= -1e-15) and idx.size >= 1
+        # the committed plastic strain is the slips along the final signs
+        np.testing.assert_allclose(ep, np.einsum("a,aij->ij", x * np.sign(tau[idx]), P[idx]), atol=1e-15)
