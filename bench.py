@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--edge", type=int, default=None,
                    help="3D workloads: lattice edge (default 1024, or 512 for 3d-cp); grains scale with the volume")
     p.add_argument("--workload", choices=["3d", "2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
-                                          "texture3d", "texture-seeds", "3d-eq", "aniso"], default="3d",
+                                          "texture3d", "texture-seeds", "3d-eq", "aniso", "mcp-vs-det"], default="3d",
                    help="3d: 1024^3 plasticity-driven hybrid (default line); 2d: 4096^2 Moore; 3d-cp: 512^3 "
                         "plasticity-driven whole job; ensemble: 256 replicas; surrogate: 1024^3 plain vs surrogate "
                         "time-to-texture; texture-seeds: both arms over 8 seeds each")
@@ -66,7 +66,8 @@ def parse():
     a = p.parse_args()
     if a.mcs is None:
         a.mcs = {"3d": 50, "2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20,
-                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500, "aniso": 200}[a.workload]
+                 "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500, "aniso": 200,
+                 "mcp-vs-det": 0}[a.workload]
     return a
 
 
@@ -892,12 +893,115 @@ def run_aniso(args):
     print(json.dumps({"workload": "aniso-2d-1024-moore8-g625-read-shockley", "mcs": args.mcs, "kT": 0.6, **out}))
 
 
+def run_mcp_vs_det(args):
+    """Sec. 2, Fig. 1 at scale: the Monte Carlo plasticity against the deterministic
+    multi-slip model (FP64, pseudo-inverse of the active constraints).  (1) Speed:
+    10^6 material points of random orientation, 20 Taylor increments of 1e-4 from
+    rest (the hybrid's refresh load), point-increments/s of each kernel.  (2)
+    Agreement: 4096 orientations, 2000 increments of 1e-6 (the paper's test),
+    sample-frame sigma_xx of both models every increment."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm, synth
+    build.build()
+    torch.cuda.set_device(0)
+    T = synth.TABLE1
+    out = {}
+    rng = np.random.default_rng(1007)
+    for P, e, n, tag in ((1_000_000, 1e-4, 20, "speed"), (4096, 1e-6, 2000, "agreement")):
+        q = rng.normal(size=(P, 4)).astype(np.float32)
+        q /= np.linalg.norm(q, axis=1, keepdims=True)
+        quat = torch.from_numpy(q).cuda()
+        grain = torch.arange(P, dtype=torch.int32, device="cuda")
+        prm = hm.cp_params(T["C11"], T["C12"], T["C44"], T["tau0"], T["taus"], T["h0"], T["beta"], e)
+        mep, mgm, mg = (torch.empty(6 * P, device="cuda"), torch.empty(P, device="cuda"),
+                        torch.empty(P, device="cuda"))
+        dep, dgm = torch.empty(6 * P, dtype=torch.float64, device="cuda"), torch.empty(P, dtype=torch.float64,
+                                                                                       device="cuda")
+        ms = torch.empty(6 * P, device="cuda")
+        ds = torch.empty(6 * P, dtype=torch.float64, device="cuda")
+        na = torch.empty(P, dtype=torch.int32, device="cuda")
+        if tag == "speed":
+            times = {}
+            for rep in range(3):
+                for model in ("mcp", "det"):
+                    hm.hp_cp_reset(prm, P, mep, mgm, mg)
+                    hm.hp_det_reset(P, dep, dgm)
+                    torch.cuda.synchronize()
+                    e0, e1 = _events(torch)
+                    e0.record()
+                    if model == "mcp":
+                        hm.hp_cp_step(prm, 7, grain, quat, 0, n, mep, mgm, mg, sigma=ms)
+                    else:
+                        hm.hp_det_step(prm, grain, quat, 0, n, dep, dgm, sigma=ds, n_active=na)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if rep:
+                        times.setdefault(model, []).append(e0.elapsed_time(e1))
+            act = na.cpu().numpy()
+            out[tag] = {"points": P, "increments": n, "e": e,
+                        "mcp_point_increments_per_s": round(P * n / (np.median(times["mcp"]) / 1e3), 1),
+                        "det_point_increments_per_s": round(P * n / (np.median(times["det"]) / 1e3), 1),
+                        "mcp_ms": round(float(np.median(times["mcp"])), 3),
+                        "det_ms": round(float(np.median(times["det"])), 3),
+                        "det_active_systems_hist": np.bincount(act[act >= 0], minlength=9)[:9].tolist(),
+                        "det_unsettled": int((act < 0).sum())}
+            out[tag]["det_over_mcp_time"] = round(out[tag]["det_ms"] / out[tag]["mcp_ms"], 2)
+        else:
+            hm.hp_cp_reset(prm, P, mep, mgm, mg)
+            hm.hp_det_reset(P, dep, dgm)
+            R = torch.from_numpy(np.stack([_rot_np(v) for v in q])).cuda()
+            r0 = R[:, 0, :]
+
+            def sxx(v):
+                v = v.view(6, P).double()
+                return (r0[:, 0] ** 2 * v[0] + r0[:, 1] ** 2 * v[1] + r0[:, 2] ** 2 * v[2] +
+                        2 * (r0[:, 1] * r0[:, 2] * v[3] + r0[:, 0] * r0[:, 2] * v[4] + r0[:, 0] * r0[:, 1] * v[5]))
+
+            Dc, Mc, Ac = [], [], []
+            for t in range(n):
+                hm.hp_det_step(prm, grain, quat, t, 1, dep, dgm, sigma=ds, n_active=na)
+                hm.hp_cp_step(prm, 13, grain, quat, t, 1, mep, mgm, mg, sigma=ms)
+                Dc.append(sxx(ds))
+                Mc.append(sxx(ms))
+                Ac.append(na.clone())
+            torch.cuda.synchronize()
+            D = torch.stack(Dc).cpu().numpy()
+            M = torch.stack(Mc).cpu().numpy()
+            A = torch.stack(Ac).cpu().numpy()
+            rel = (M - D) / D
+            multi = A >= 2
+            means = np.array([rel[multi[:, i], i].mean() for i in range(P) if multi[:, i].sum() > 200])
+            out[tag] = {"orientations": P, "increments": n, "e": e,
+                        "multi_slip_mean_rel_dev": round(float(means.mean()), 5),
+                        "multi_slip_mean_rel_dev_q05_q95": [round(float(np.quantile(means, 0.05)), 5),
+                                                            round(float(np.quantile(means, 0.95)), 5)],
+                        "orientations_with_multi_slip": int(means.size),
+                        "max_active_systems": int(A.max()), "det_unsettled": int((A < 0).sum()),
+                        "curve_orientation0_MPa_every_200": {
+                            "strain": [round((t + 1) * e, 6) for t in range(0, n, 200)],
+                            "det": [round(float(D[t, 0]), 4) for t in range(0, n, 200)],
+                            "mcp": [round(float(M[t, 0]), 4) for t in range(0, n, 200)]}}
+        del mep, mgm, mg, dep, dgm, ms, ds, na
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "mcp-vs-det-ni-single-crystals", "material": "Table 1 nickel", **out}))
+
+
+def _rot_np(q):
+    q = np.asarray(q, np.float64)
+    q = q / np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
 def main():
     args = parse()
     if args.impl == "ours" and args.workload not in ("3d",):
         {"2d": run_2d, "3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
          "sweep3d": run_sweep3d, "texture2d": run_texture, "texture3d": run_texture,
-         "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq, "aniso": run_aniso}[args.workload](args)
+         "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq, "aniso": run_aniso,
+         "mcp-vs-det": run_mcp_vs_det}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

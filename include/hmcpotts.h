@@ -463,6 +463,46 @@ HP_API int hp_cp_step_strain(const hp_cp_params* prm, uint64_t seed, const int32
                              uint32_t t, const float* eps_total, hp_cp_state* st, float* sigma, float* w, float* erho,
                              int32_t* b, void* stream);
 
+/* Deterministic rate-independent multi-slip crystal plasticity: the model the
+ * Monte Carlo plasticity is checked against (Sec. 2, Fig. 1, a nickel single
+ * crystal; the ill-conditioned constraint equations of the active systems are
+ * solved with a singular value decomposition).  FP64, one thread per point.
+ * Per increment (crystal frame, prm C11 C12 C44 tau0 taus h0, Voce hardening
+ * g(gamma) as for hp_cp_step; beta, G, energy_scale and w_weight unused):
+ * trial stress C : (eps - eps_p), active set {a : |tau_a| - g(gamma) > tol},
+ * tol = 1e-12 tau0; Newton on |tau_a| - sum_b s_a s_b P_a:C:P_b x_b =
+ * g(gamma + sum x) with the Moore-Penrose inverse of the constraint matrix
+ * (eigenvalues at or below 1e-10 of the largest discarded); drop systems whose
+ * slip comes out negative, add systems whose resolved shear then exceeds g,
+ * repeat; commit eps_p += sum x_a s_a P_a, gamma += sum x_a.
+ * State, device memory: eps_p double[6][P] (xx yy zz yz xz xy, crystal frame),
+ * gamma double[P].                                                           */
+typedef struct {
+    int64_t P;
+    double* eps_p;
+    double* gamma;
+} hp_det_state;
+
+/* Zero plastic strain and accumulated slip.                                  */
+HP_API int hp_det_reset(hp_det_state* st, void* stream);
+
+/* Load increments t = t0+1 .. t0+n_incr of the prescribed strain
+ * t e_incr diag(1,-1/2,-1/2) (sample frame, as hp_cp_step); point p has the
+ * orientation quat[4*grain[p]].  Afterwards sigma (device double[6][P],
+ * crystal frame; NULL to skip) holds the stress and n_active (device int32[P],
+ * NULL to skip) the number of active systems of the last increment, or -1 when
+ * the active set did not settle within 50 passes: that point's state is then
+ * left as before the failing increment and its later increments are skipped.
+ * Asynchronous on stream.                                                    */
+HP_API int hp_det_step(const hp_cp_params* prm, const int32_t* grain, const float* quat, uint32_t t0,
+                       int32_t n_incr, hp_det_state* st, double* sigma, int32_t* n_active, void* stream);
+
+/* One increment to each point's own total strain (sample frame, device
+ * float[6][P], e.g. from hp_elastic_solve); otherwise as hp_det_step.       */
+HP_API int hp_det_step_strain(const hp_cp_params* prm, const int32_t* grain, const float* quat,
+                              const float* eps_total, hp_det_state* st, double* sigma, int32_t* n_active,
+                              void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Learned field surrogate: 11 -> 64 -> 64 -> 64 -> 2 perceptron with GELU,    */
 /* BF16 operands and FP32 accumulation on the tensor cores.  It maps a grain's */

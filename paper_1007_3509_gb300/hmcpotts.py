@@ -82,6 +82,10 @@ class hp_cp_state(C.Structure):
     _fields_ = [("P", C.c_int64), ("eps_p", C.c_void_p), ("gamma", C.c_void_p), ("g", C.c_void_p)]
 
 
+class hp_det_state(C.Structure):
+    _fields_ = [("P", C.c_int64), ("eps_p", C.c_void_p), ("gamma", C.c_void_p)]
+
+
 _SIGS = {
     "hp_last_error_message": ([], C.c_char_p),
     "hp_version": ([], C.c_char_p),
@@ -131,6 +135,11 @@ _SIGS = {
     "hp_elastic_solve": ([C.POINTER(hp_cp_params), C.POINTER(hp_elastic_params), C.c_void_p, C.c_void_p, C.c_void_p,
                           C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                           C.c_void_p], C.c_int),
+    "hp_det_reset": ([C.POINTER(hp_det_state), C.c_void_p], C.c_int),
+    "hp_det_step": ([C.POINTER(hp_cp_params), C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
+                     C.POINTER(hp_det_state), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hp_det_step_strain": ([C.POINTER(hp_cp_params), C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.POINTER(hp_det_state), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_cp_step_strain": ([C.POINTER(hp_cp_params), C.c_uint64, C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p,
                            C.POINTER(hp_cp_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_set_anisotropy": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
@@ -423,6 +432,34 @@ def hp_cp_step_strain(prm, seed, grain, quat, t, eps_total, eps_p, gamma, g, sig
                                    _dev(eps_total, 6 * P, 4, nm + " eps_total"), C.byref(st),
                                    _dev(sigma, 6 * P, 4, nm + " sigma"), _dev(w, P, 4, nm + " w"),
                                    _dev(erho, P, 4, nm + " erho"), _dev(b, P, 4, nm + " b"), _stream(stream)))
+
+
+def _det_state(P, eps_p, gamma, who):
+    return hp_det_state(P, _dev(eps_p, 6 * P, 8, who + " eps_p"), _dev(gamma, P, 8, who + " gamma"))
+
+
+def hp_det_reset(P, eps_p, gamma, stream=None):
+    st = _det_state(int(P), eps_p, gamma, "hp_det_reset")
+    _check(lib().hp_det_reset(C.byref(st), _stream(stream)))
+
+
+def hp_det_step(prm, grain, quat, t0, n_incr, eps_p, gamma, sigma=None, n_active=None, stream=None):
+    """Deterministic multi-slip increments t0+1 .. t0+n_incr (FP64 state: eps_p
+    double[6 P], gamma double[P]; sigma double[6 P] and n_active int32[P] optional)."""
+    P, wh = int(grain.numel()), "hp_det_step"
+    st = _det_state(P, eps_p, gamma, wh)
+    _check(lib().hp_det_step(C.byref(prm), _dev(grain, P, 4, wh + " grain"), _dev(quat, 0, 4, wh + " quat"),
+                             C.c_uint32(t0), int(n_incr), C.byref(st), _dev(sigma, 6 * P, 8, wh + " sigma"),
+                             _dev(n_active, P, 4, wh + " n_active"), _stream(stream)))
+
+
+def hp_det_step_strain(prm, grain, quat, eps_total, eps_p, gamma, sigma=None, n_active=None, stream=None):
+    P, wh = int(grain.numel()), "hp_det_step_strain"
+    st = _det_state(P, eps_p, gamma, wh)
+    _check(lib().hp_det_step_strain(C.byref(prm), _dev(grain, P, 4, wh + " grain"), _dev(quat, 0, 4, wh + " quat"),
+                                    _dev(eps_total, 6 * P, 4, wh + " eps_total"), C.byref(st),
+                                    _dev(sigma, 6 * P, 8, wh + " sigma"), _dev(n_active, P, 4, wh + " n_active"),
+                                    _stream(stream)))
 
 
 def hp_build_read_shockley(J_max, theta_max, bin_w, nbins, unit_per_degree, mobility=False):

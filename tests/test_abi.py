@@ -129,3 +129,22 @@ def test_si_links_invert_eq8(hm):
     assert abs(hm.hp_si_links(gamma_s, m10, l0, gamma_mc, m_mc, Delta, J, tau)["seconds_per_mcs"] - 600.0) < 1e-9
     with pytest.raises(hm.HPError):
         hm.hp_si_links(0.0, m_s, l0, gamma_mc, m_mc)
+
+
+def test_det_argument_errors(hm):
+    """The deterministic comparator validates its arguments before any device work."""
+    import ctypes as C
+    T = dict(C11=250.8e3, C12=150.0e3, C44=123.5e3, tau0=8.0, taus=122.0, h0=440.0, beta=1000.0)
+    prm = hm.cp_params(T["C11"], T["C12"], T["C44"], T["tau0"], T["taus"], T["h0"], T["beta"], 1e-6)
+    dummy = C.c_void_p(16)
+    st = hm.hp_det_state(0, dummy, dummy)  # no points
+    assert hm.lib().hp_det_step(C.byref(prm), dummy, dummy, 0, 1, C.byref(st), None, None, None) == hm.HP_ERR_ARG
+    st = hm.hp_det_state(4, None, dummy)  # no plastic-strain buffer
+    assert hm.lib().hp_det_step(C.byref(prm), dummy, dummy, 0, 1, C.byref(st), None, None, None) == hm.HP_ERR_ARG
+    assert hm.lib().hp_det_reset(C.byref(st), None) == hm.HP_ERR_ARG
+    st = hm.hp_det_state(4, dummy, dummy)
+    assert hm.lib().hp_det_step(C.byref(prm), dummy, dummy, 0, -1, C.byref(st), None, None, None) == hm.HP_ERR_ARG
+    bad = hm.cp_params(T["C12"], T["C11"], T["C44"], T["tau0"], T["taus"], T["h0"], T["beta"], 1e-6)  # C11 < C12
+    assert hm.lib().hp_det_step(C.byref(bad), dummy, dummy, 0, 1, C.byref(st), None, None, None) == hm.HP_ERR_ARG
+    assert hm.lib().hp_det_step_strain(C.byref(prm), dummy, dummy, None, C.byref(st), None, None, None) == \
+        hm.HP_ERR_ARG
