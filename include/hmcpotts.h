@@ -523,6 +523,11 @@ HP_API int hp_mlp_forward(const float* params, const float* X, int64_t M, float*
  * float, may be NULL) = L for L = 1/(2M) sum_rows sum_outputs (y - t)^2.      */
 HP_API int hp_mlp_gradients(const float* params, const float* X, const float* T, int64_t M, float* grads,
                             float* loss, void* stream);
+/* The network's activation as the kernels evaluate it, for testing: g[i] =
+ * GELU(z[i]) = z Phi(z) and dg[i] = Phi(z) + z phi(z) (device float[n] each),
+ * Phi through erf by Abramowitz and Stegun 7.1.26 (|error| <= 1.5e-7).       */
+HP_API int hp_debug_gelu(const float* z, int64_t n, float* g, float* dg, void* stream);
+
 /* One Adam step (Kingma & Ba) on the FP32 master weights: m, v (device float
  * [param_count]) are the moment estimates, step counts from 1.               */
 HP_API int hp_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr, float beta1,

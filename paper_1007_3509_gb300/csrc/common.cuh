@@ -122,4 +122,20 @@ int orientations_run(int32_t G, uint64_t seed, int32_t kind, float* orient, cuda
 // raised exactly as by a kernel that timed out.
 int lean_wait_probe(long long limit, int late, cudaStream_t s);
 int mlp_wait_probe(long long limit, int late, cudaStream_t s);
+
+// Training state of one hp_sur_train call: the packed weight image and the
+// per-CTA gradient slots, owned by the call.
+struct MlpTrain {
+    unsigned char* img = nullptr;
+    float* part = nullptr;
+    int64_t grid = 0;  // CTAs of the gradient kernel for a batch of `rows`
+    int64_t rows = 0;
+};
+// allocates the buffers for batches of `rows` rows and packs params
+int mlp_train_begin(const float* params, int64_t rows, MlpTrain* t, cudaStream_t s);
+// gradients of the batch (X, Y: t->rows rows) and the Adam step `step`;
+// *loss (device, may be null) receives the batch loss
+int mlp_train_step(MlpTrain* t, float* params, float* m, float* v, const float* X, const float* Y, int32_t step,
+                   float lr, float beta1, float beta2, float eps, float* loss, cudaStream_t s);
+void mlp_train_end(MlpTrain* t, cudaStream_t s);
 }  // namespace hp

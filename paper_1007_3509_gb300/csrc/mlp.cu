@@ -138,9 +138,31 @@ __device__ __forceinline__ int canon(int r, int k, int K) {
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// Standard normal distribution Phi(z) and density phi(z).  erf(x) for x >= 0
+// by the rational approximation of Abramowitz and Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26 (Hastings): erf(x) = 1 - t (a1 + t (a2 +
+// t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1/(1 + p x), |error| <= 1.5e-7; odd
+// in x.  Its exp(-x^2) with x = |z|/sqrt2 is exp(-z^2/2), which phi reuses.
+__device__ __forceinline__ void ncdf_pdf(float z, float& cdf, float& pdf) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float e = __expf(-x * x);
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float er = fmaf(-poly, e, 1.0f);  // erf(|z| / sqrt2)
+    cdf = fmaf(0.5f, copysignf(er, z), 0.5f);
+    pdf = 0.39894228040143268f * e;
+}
+// GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu(float z) {
+    float c, d;
+    ncdf_pdf(z, c, d);
+    return z * c;
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    float c, d;
+    ncdf_pdf(z, c, d);
+    return fmaf(z, d, c);
 }
 
 // write a full row of K values (K multiple of 8) into a K-major operand
@@ -379,9 +401,63 @@ __device__ __forceinline__ void tmem_ldw(uint32_t taddr, float* v) {
     }
 }
 
-__global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ P, const float* __restrict__ X,
-                                                      const float* __restrict__ T, int64_t M, float inv_batch,
-                                                      float* __restrict__ grads, float* __restrict__ loss, int* err) {
+// The packed weight image: the BF16 operands of TrainSmem (w1 .. w3t, in that
+// order and layout) followed by the FP32 biases and output layer
+// (b1, b2, b3, bf16-rounded W4, b4).  Built from the FP32 parameters by
+// k_mlp_pack and rewritten by the fused reduce + Adam kernel after every step.
+constexpr int IMG_BF = 2 * (HID * INP + 4 * HID * HID);  // bytes of BF16 operands
+constexpr int IMG_F = 3 * HID + OUT * HID + OUT;         // floats after them
+constexpr size_t IMG_BYTES = ((size_t)IMG_BF + 4 * IMG_F + 15) / 16 * 16;
+// per-CTA gradient slot: NPARAM gradients then the CTA's share of the loss
+constexpr int PSTR = (NPARAM + 1 + 3) / 4 * 4;
+static_assert(offsetof(TrainSmem, w1) == 0 && offsetof(TrainSmem, w2) == 2 * HID * INP &&
+                  offsetof(TrainSmem, w3t) + 2 * HID * HID == IMG_BF,
+              "the BF16 operands are one block at the start of TrainSmem");
+
+// write parameter i (value p) into the packed image
+__device__ __forceinline__ void pack_param(unsigned char* img, int i, float p) {
+    float* f = reinterpret_cast<float*>(img + IMG_BF);
+    const __nv_bfloat16 h = __float2bfloat16_rn(p);
+    unsigned char* w2 = img + 2 * HID * INP;
+    unsigned char* w3 = w2 + 2 * HID * HID;
+    unsigned char* w2t = w3 + 2 * HID * HID;
+    unsigned char* w3t = w2t + 2 * HID * HID;
+    if (i < OB1) {
+        *reinterpret_cast<__nv_bfloat16*>(img + canon(i / IN, i % IN, INP)) = h;
+    } else if (i < OW2) {
+        f[i - OB1] = p;
+    } else if (i < OB2) {
+        const int t = i - OW2, n = t / HID, k = t - n * HID;
+        *reinterpret_cast<__nv_bfloat16*>(w2 + canon(n, k, HID)) = h;
+        *reinterpret_cast<__nv_bfloat16*>(w2t + canon(k, n, HID)) = h;
+    } else if (i < OW3) {
+        f[HID + i - OB2] = p;
+    } else if (i < OB3) {
+        const int t = i - OW3, n = t / HID, k = t - n * HID;
+        *reinterpret_cast<__nv_bfloat16*>(w3 + canon(n, k, HID)) = h;
+        *reinterpret_cast<__nv_bfloat16*>(w3t + canon(k, n, HID)) = h;
+    } else if (i < OW4) {
+        f[2 * HID + i - OB3] = p;
+    } else if (i < OB4) {
+        f[3 * HID + i - OW4] = bf16r(p);
+    } else {
+        f[3 * HID + OUT * HID + i - OB4] = p;
+    }
+}
+
+__global__ void k_mlp_pack(const float* __restrict__ P, unsigned char* __restrict__ img) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NPARAM) pack_param(img, i, P[i]);
+    if (i < HID * (INP - IN)) {  // zero padding of the first layer's K
+        const int n = i / (INP - IN), k = IN + i % (INP - IN);
+        *reinterpret_cast<__nv_bfloat16*>(img + canon(n, k, INP)) = __float2bfloat16_rn(0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(NTT, 1) k_mlp_train(const unsigned char* __restrict__ img,
+                                                      const float* __restrict__ X, const float* __restrict__ T,
+                                                      int64_t M, float inv_batch, float* __restrict__ part, int* err) {
+
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -394,32 +470,27 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         mbar_init(saddr(&S.mbar));
         S.loss = 0.0f;
     }
-    for (int idx = tid; idx < HID * INP; idx += NTT) {
-        const int n = idx / INP, k = idx - n * INP;
-        *reinterpret_cast<__nv_bfloat16*>(S.w1 + canon(n, k, INP)) = __float2bfloat16_rn(k < IN ? P[OW1 + n * IN + k] : 0.0f);
-    }
-    for (int idx = tid; idx < HID * HID; idx += NTT) {
-        const int n = idx / HID, k = idx - n * HID;
-        *reinterpret_cast<__nv_bfloat16*>(S.w2 + canon(n, k, HID)) = __float2bfloat16_rn(P[OW2 + n * HID + k]);
-        *reinterpret_cast<__nv_bfloat16*>(S.w3 + canon(n, k, HID)) = __float2bfloat16_rn(P[OW3 + n * HID + k]);
-        *reinterpret_cast<__nv_bfloat16*>(S.w2t + canon(n, k, HID)) = __float2bfloat16_rn(P[OW2 + k * HID + n]);
-        *reinterpret_cast<__nv_bfloat16*>(S.w3t + canon(n, k, HID)) = __float2bfloat16_rn(P[OW3 + k * HID + n]);
+    {   // the BF16 operands are one contiguous block at the start of TrainSmem
+        const int4* src = reinterpret_cast<const int4*>(img);
+        int4* dst = reinterpret_cast<int4*>(S.w1);
+        for (int i = tid; i < IMG_BF / 16; i += NTT) dst[i] = __ldg(src + i);
+        const float* f = reinterpret_cast<const float*>(img + IMG_BF);
+        for (int i = tid; i < HID; i += NTT) {
+            S.b1[i] = f[i];
+            S.b2[i] = f[HID + i];
+            S.b3[i] = f[2 * HID + i];
+            S.gb1[i] = S.gb2[i] = S.gb3[i] = 0.0f;
+        }
+        for (int i = tid; i < OUT * HID; i += NTT) {
+            S.w4[i] = f[3 * HID + i];
+            S.gw4[i] = 0.0f;
+        }
+        if (tid < OUT) {
+            S.b4[tid] = f[3 * HID + OUT * HID + tid];
+            S.gb4[tid] = 0.0f;
+        }
     }
     for (int i = tid; i < TILE * TILE * 2 / 16; i += NTT) reinterpret_cast<int4*>(S.dzt)[i] = make_int4(0, 0, 0, 0);
-    for (int i = tid; i < HID; i += NTT) {
-        S.b1[i] = P[OB1 + i];
-        S.b2[i] = P[OB2 + i];
-        S.b3[i] = P[OB3 + i];
-        S.gb1[i] = S.gb2[i] = S.gb3[i] = 0.0f;
-    }
-    for (int i = tid; i < OUT * HID; i += NTT) {
-        S.w4[i] = bf16r(P[OW4 + i]);
-        S.gw4[i] = 0.0f;
-    }
-    if (tid < OUT) {
-        S.b4[tid] = P[OB4 + tid];
-        S.gb4[tid] = 0.0f;
-    }
     sync_for_mma();
     const uint32_t tm = S.tmem;
     const uint32_t mbar = saddr(&S.mbar);
@@ -592,25 +663,28 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         if (!(ok = wait_mma())) break;
         first = 0;
     }
-    // ---- flush this CTA's gradients ------------------------------------------
+    // ---- this CTA's gradients to its slot (plain stores; every entry written) --
     if (ok && !first) {
+        float* slot = part + (size_t)blockIdx.x * PSTR;
         // weight gradients: TMEM lanes 0..63 (quadrants 0 and 1) hold dW rows
-        // (out features); each half of the warps takes 32 of the columns
+        // (out features); each group of four warps takes FW of the columns
         if (quad < 2) {
             const int o = r;  // out feature
             tmem_ldw(lb + CDW3, v);
 #pragma unroll
-            for (int k = 0; k < FW; ++k) atomicAdd(&grads[OW3 + o * HID + f0 + k], v[k]);
+            for (int k = 0; k < FW; k += 4)
+                *reinterpret_cast<float4*>(slot + OW3 + o * HID + f0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
             tmem_ldw(lb + CDW2, v);
 #pragma unroll
-            for (int k = 0; k < FW; ++k) atomicAdd(&grads[OW2 + o * HID + f0 + k], v[k]);
+            for (int k = 0; k < FW; k += 4)
+                *reinterpret_cast<float4*>(slot + OW2 + o * HID + f0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
             if (hf == 0) {
                 tmem_ldw(lb + CDW1, v);  // the first 16 columns hold dW1
 #pragma unroll
-                for (int k = 0; k < IN; ++k) atomicAdd(&grads[OW1 + o * IN + k], v[k]);
+                for (int k = 0; k < IN; ++k) slot[OW1 + o * IN + k] = v[k];
             }
         }
-        // per-row reductions of the loss and b4 gradient (the second half adds zeros)
+        // per-row reductions of the loss and b4 gradient (the other groups add zeros)
         for (int m = 16; m >= 1; m >>= 1) {
             my_loss += __shfl_xor_sync(0xFFFFFFFFu, my_loss, m);
             gb4_0 += __shfl_xor_sync(0xFFFFFFFFu, gb4_0, m);
@@ -623,13 +697,13 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const float* __restrict__ 
         }
         __syncthreads();
         for (int i = tid; i < HID; i += NTT) {
-            atomicAdd(&grads[OB1 + i], S.gb1[i]);
-            atomicAdd(&grads[OB2 + i], S.gb2[i]);
-            atomicAdd(&grads[OB3 + i], S.gb3[i]);
+            slot[OB1 + i] = S.gb1[i];
+            slot[OB2 + i] = S.gb2[i];
+            slot[OB3 + i] = S.gb3[i];
         }
-        for (int i = tid; i < OUT * HID; i += NTT) atomicAdd(&grads[OW4 + i], S.gw4[i]);
-        if (tid < OUT) atomicAdd(&grads[OB4 + tid], S.gb4[tid]);
-        if (tid == 0 && loss) atomicAdd(loss, S.loss * 0.5f * inv_batch);
+        for (int i = tid; i < OUT * HID; i += NTT) slot[OW4 + i] = S.gw4[i];
+        if (tid < OUT) slot[OB4 + tid] = S.gb4[tid];
+        if (tid == 0) slot[NPARAM] = S.loss * 0.5f * inv_batch;
     }
     if (!ok) drain_after_timeout(mbar, phase, err);
     fence_before();
@@ -649,6 +723,62 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ g, float
     m[i] = mi;
     v[i] = vi;
     P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Sum of entry i over the nslots gradient slots, by the 8 consecutive lanes
+// of a group (lane j of the group takes slots j, j + 8, ...; a fixed shuffle
+// tree then adds the eight partial sums, so the order never varies).
+__device__ __forceinline__ float slot_sum(const float* __restrict__ part, int nslots, int i) {
+    const int j = threadIdx.x & 7;
+    float acc = 0.0f;
+    if (i <= NPARAM)
+        for (int c = j; c < nslots; c += 8) acc += part[(size_t)c * PSTR + i];
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+    return acc;
+}
+
+constexpr int kRedT = 256, kRedPer = kRedT / 8;  // entries per block
+constexpr int kRedBlocks = (NPARAM + 1 + kRedPer - 1) / kRedPer;
+
+// gradients (and the loss, entry NPARAM) of a batch from its slots
+__global__ void __launch_bounds__(kRedT) k_mlp_reduce(const float* __restrict__ part, int nslots,
+                                                      float* __restrict__ grads, float* __restrict__ loss) {
+    const int i = blockIdx.x * kRedPer + (threadIdx.x >> 3);
+    const float g = slot_sum(part, nslots, i);
+    if ((threadIdx.x & 7) == 0) {
+        if (i < NPARAM) grads[i] = g;
+        if (i == NPARAM && loss) *loss = g;
+    }
+}
+
+// One training step's update: the slots summed (as k_mlp_reduce), Adam (as
+// k_adam) and the new parameter written into the packed image for the next step.
+__global__ void __launch_bounds__(kRedT) k_mlp_reduce_adam(const float* __restrict__ part, int nslots,
+                                                           float* __restrict__ P, float* __restrict__ m,
+                                                           float* __restrict__ v, unsigned char* __restrict__ img,
+                                                           float* __restrict__ loss, float lr, float b1, float b2,
+                                                           float eps, float c1, float c2) {
+    const int i = blockIdx.x * kRedPer + (threadIdx.x >> 3);
+    const float gi = slot_sum(part, nslots, i);
+    if ((threadIdx.x & 7) != 0) return;
+    if (i == NPARAM && loss) *loss = gi;
+    if (i >= NPARAM) return;
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float p = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    P[i] = p;
+    pack_param(img, i, p);
+}
+
+__global__ void k_gelu_eval(const float* __restrict__ z, int64_t n, float* __restrict__ g, float* __restrict__ dg) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    g[i] = gelu(z[i]);
+    dg[i] = gelu_grad(z[i]);
 }
 
 int g_err_dev = -1;
@@ -728,6 +858,79 @@ extern "C" int hp_mlp_forward(const float* params, const float* X, int64_t M, fl
     return HP_OK;
 }
 
+namespace hp {
+namespace {
+int train_configure() {
+    static bool configured = false;
+    if (!configured) {
+        HP_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(TrainSmem) + 1024)));
+        configured = true;
+    }
+    return HP_OK;
+}
+
+int64_t train_grid(int64_t M) {
+    const int64_t tiles = (M + TILE - 1) / TILE;
+    return tiles < sm_count() ? tiles : sm_count();
+}
+
+int launch_train(const unsigned char* img, const float* X, const float* T, int64_t M, float* part, int* err,
+                 cudaStream_t s) {
+    ::hp::count_launch();
+    k_mlp_train<<<(unsigned)train_grid(M), NTT, sizeof(TrainSmem) + 1024, s>>>(img, X, T, M, 1.0f / (float)M, part,
+                                                                              err);
+    HP_LAUNCH_CHECK("k_mlp_train");
+    return HP_OK;
+}
+
+int launch_pack(const float* params, unsigned char* img, cudaStream_t s) {
+    ::hp::count_launch();
+    k_mlp_pack<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, img);
+    HP_LAUNCH_CHECK("k_mlp_pack");
+    return HP_OK;
+}
+}  // namespace
+
+int mlp_train_begin(const float* params, int64_t rows, MlpTrain* t, cudaStream_t s) {
+    if (!params || rows < 1 || !t) return set_error(HP_ERR_ARG, "mlp_train_begin: bad arguments");
+    int rc = train_configure();
+    if (rc) return rc;
+    t->rows = rows;
+    t->grid = train_grid(rows);
+    if (cudaMallocAsync((void**)&t->img, IMG_BYTES, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&t->part, sizeof(float) * (size_t)PSTR * (size_t)t->grid, s) != cudaSuccess) {
+        mlp_train_end(t, s);
+        return set_error(HP_ERR_OOM, "mlp_train_begin: allocation failed");
+    }
+    return launch_pack(params, t->img, s);
+}
+
+int mlp_train_step(MlpTrain* t, float* params, float* m, float* v, const float* X, const float* Y, int32_t step,
+                   float lr, float beta1, float beta2, float eps, float* loss, cudaStream_t s) {
+    if (!t || !t->img || !t->part || step < 1) return set_error(HP_ERR_ARG, "mlp_train_step: bad arguments");
+    int* err = nullptr;
+    int rc = error_flag(&err);
+    if (rc) return rc;
+    rc = launch_train(t->img, X, Y, t->rows, t->part, err, s);
+    if (rc) return rc;
+    const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+    ::hp::count_launch();
+    k_mlp_reduce_adam<<<kRedBlocks, kRedT, 0, s>>>(t->part, (int)t->grid, params, m, v, t->img, loss, lr, beta1, beta2,
+                                                   eps, c1, c2);
+    HP_LAUNCH_CHECK("k_mlp_reduce_adam");
+    return HP_OK;
+}
+
+void mlp_train_end(MlpTrain* t, cudaStream_t s) {
+    if (!t) return;
+    if (t->img) cudaFreeAsync(t->img, s);
+    if (t->part) cudaFreeAsync(t->part, s);
+    t->img = nullptr;
+    t->part = nullptr;
+}
+}  // namespace hp
+
 extern "C" int hp_mlp_gradients(const float* params, const float* X, const float* T, int64_t M, float* grads,
                                 float* loss, void* stream) {
     if (!params || !X || !T || !grads || M < 1) return set_error(HP_ERR_ARG, "hp_mlp_gradients: bad arguments");
@@ -735,19 +938,25 @@ extern "C" int hp_mlp_gradients(const float* params, const float* X, const float
     int rc = error_flag(&err);
     if (rc) return rc;
     cudaStream_t s = as_stream(stream);
-    HP_CUDA(cudaMemsetAsync(grads, 0, sizeof(float) * NPARAM, s));
-    if (loss) HP_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), s));
-    const size_t smem = sizeof(TrainSmem) + 1024;
-    static bool configured = false;
-    if (!configured) {
-        HP_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
+    MlpTrain t;
+    rc = mlp_train_begin(params, M, &t, s);
+    if (rc == HP_OK) rc = launch_train(t.img, X, T, M, t.part, err, s);
+    if (rc == HP_OK) {
+        ::hp::count_launch();
+        k_mlp_reduce<<<kRedBlocks, kRedT, 0, s>>>(t.part, (int)t.grid, grads, loss);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error(e, "k_mlp_reduce");
     }
-    const int64_t tiles = (M + TILE - 1) / TILE;
-    const int64_t grid = tiles < sm_count() ? tiles : sm_count();
+    mlp_train_end(&t, s);
+    return rc;
+}
+
+extern "C" int hp_debug_gelu(const float* z, int64_t n, float* g, float* dg, void* stream) {
+    if (!z || !g || !dg || n < 0) return set_error(HP_ERR_ARG, "hp_debug_gelu: bad arguments");
+    if (n == 0) return HP_OK;
     ::hp::count_launch();
-    k_mlp_train<<<(unsigned)grid, NTT, smem, s>>>(params, X, T, M, 1.0f / (float)M, grads, loss, err);
-    HP_LAUNCH_CHECK("k_mlp_train");
+    k_gelu_eval<<<(unsigned)((n + 255) / 256), 256, 0, as_stream(stream)>>>(z, n, g, dg);
+    HP_LAUNCH_CHECK("k_gelu_eval");
     return HP_OK;
 }
 

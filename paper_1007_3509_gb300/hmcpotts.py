@@ -152,6 +152,7 @@ _SIGS = {
     "hp_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
     "hp_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p],
                          C.c_int),
+    "hp_debug_gelu": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hp_mlp_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_float,
                      C.c_float, C.c_void_p], C.c_int),
     "hp_mlp_status": ([C.POINTER(C.c_int32)], C.c_int),
@@ -325,6 +326,12 @@ def hp_mlp_gradients(params, X, T, grads, loss=None, stream=None):
     _check(lib().hp_mlp_gradients(_dev(params, P, 4, w + " params"), _dev(X, 11 * M, 4, w + " X"),
                                   _dev(T, 2 * M, 4, w + " T"), M, _dev(grads, P, 4, w + " grads"),
                                   _dev(loss, 1, 4, w + " loss"), _stream(stream)))
+
+
+def hp_debug_gelu(z, g, dg, stream=None):
+    n, w = int(z.numel()), "hp_debug_gelu"
+    _check(lib().hp_debug_gelu(_dev(z, n, 4, w + " z"), n, _dev(g, n, 4, w + " g"), _dev(dg, n, 4, w + " dg"),
+                               _stream(stream)))
 
 
 def hp_mlp_adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

@@ -108,8 +108,8 @@ def run_plain(torch, cfg: HybridConfig, time_it=True, coupling="taylor", el_tol=
     return out
 
 
-def train_surrogate(torch, prm, n_orient=65536, K=128, n_incr=20, steps=60000, lr=2e-3, seed=3000, log_every=0,
-                    batch=65536):
+def train_surrogate(torch, prm, n_orient=65536, K=128, n_incr=20, steps=60000, lr=3e-3, seed=3000, log_every=0,
+                    batch=19440):
     """Generate samples with the MCP kernel and fit the network with the library's training
     loop (hp_sur_train: Adam on contiguous minibatches of `batch` rows taken in turn, cosine
     learning-rate decay to 2 % of lr; rows are orientation-major, so each minibatch holds whole

@@ -125,3 +125,24 @@ def test_training_reduces_loss():
             hist.append(loss.item())
     assert hm.hp_mlp_status() == 0
     assert hist[1] < hist[0] / 10, hist
+
+
+def test_activation_within_the_erf_approximation_bound():
+    """The kernels' GELU and its derivative (erf by Abramowitz and Stegun 7.1.26,
+    |error| <= 1.5e-7, with fast exp and reciprocal) against FP64 erf: within
+    5e-7 (1 + |z|) for GELU and 5e-7 for the derivative over [-30, 30]."""
+    import math
+    torch, hm = need_gpu()
+    z = np.concatenate([np.linspace(-10, 10, 200001), [-30.0, -12.0, -1e-30, 0.0, 1e-30, 12.0, 30.0]]).astype(np.float32)
+    tz = torch.from_numpy(z).cuda()
+    g = torch.empty_like(tz)
+    dg = torch.empty_like(tz)
+    hm.hp_debug_gelu(tz, g, dg)
+    torch.cuda.synchronize()
+    zd = z.astype(np.float64)
+    cdf = np.array([0.5 * (1.0 + math.erf(v / math.sqrt(2.0))) for v in zd])
+    pdf = np.exp(-0.5 * zd * zd) / math.sqrt(2.0 * math.pi)
+    eg = np.abs(g.cpu().numpy() - zd * cdf)
+    ed = np.abs(dg.cpu().numpy() - (cdf + zd * pdf))
+    assert np.all(eg <= 5e-7 * (1.0 + np.abs(zd))), eg.max()
+    assert np.all(ed <= 5e-7), ed.max()
