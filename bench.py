@@ -57,17 +57,19 @@ def parse():
     p.add_argument("--edge", type=int, default=None,
                    help="3D workloads: lattice edge (default 1024, or 512 for 3d-cp); grains scale with the volume")
     p.add_argument("--workload", choices=["3d", "2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
-                                          "texture3d", "texture-seeds", "3d-eq", "aniso", "mcp-vs-det"], default="3d",
+                                          "texture3d", "texture-seeds", "3d-eq", "aniso", "mcp-vs-det", "surrogate-train"],
+                   default="3d",
                    help="3d: 1024^3 plasticity-driven hybrid (default line); 2d: 4096^2 Moore; 3d-cp: 512^3 "
                         "plasticity-driven whole job; ensemble: 256 replicas; surrogate: 1024^3 plain vs surrogate "
                         "time-to-texture; texture-seeds: both arms over 8 seeds each")
     p.add_argument("--seeds", type=int, default=8, help="texture-seeds: seeds per arm")
+    p.add_argument("--train-steps", type=int, default=60000, help="surrogate-train: Adam steps")
     p.add_argument("--no-autotune", action="store_true")
     a = p.parse_args()
     if a.mcs is None:
         a.mcs = {"3d": 50, "2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20,
                  "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500, "aniso": 200,
-                 "mcp-vs-det": 0}[a.workload]
+                 "mcp-vs-det": 0, "surrogate-train": 0}[a.workload]
     return a
 
 
@@ -893,6 +895,41 @@ def run_aniso(args):
     print(json.dumps({"workload": "aniso-2d-1024-moore8-g625-read-shockley", "mcs": args.mcs, "kT": 0.6, **out}))
 
 
+def run_surrogate_train(args):
+    """The surrogate's training on its own: 65536 orientations x 20 load steps of
+    plasticity samples (128 histories each), Adam on 972-orientation minibatches
+    (one wave of 128-row tiles) for --train-steps steps; time per step, and the
+    field error on 256 held-out orientations against 4096-history averages."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm, hybrid
+    build.build()
+    torch.cuda.set_device(0)
+    prm = hybrid.cp_params_table1(1e-4, 7.0)
+    hybrid.train_surrogate(torch, prm, steps=100)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    params, load, loss, _ = hybrid.train_surrogate(torch, prm, steps=args.train_steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    n_orient, K, n_incr = 256, 4096, 20
+    quat = torch.empty(n_orient, 4, device="cuda")
+    hm.hp_orientations(n_orient, 999, hm.ORIENT_SO3, quat)
+    X = torch.empty(n_orient * n_incr, 11, device="cuda")
+    Y = torch.empty(n_orient * n_incr, 2, device="cuda")
+    hm.hp_sur_generate(prm, 4242, quat, n_orient, K, n_incr, X, Y)
+    P = torch.empty_like(Y)
+    hm.hp_mlp_forward(params, X, P)
+    torch.cuda.synchronize()
+    y, pr = Y.cpu().numpy().astype(np.float64), P.cpu().numpy().astype(np.float64)
+    sw, se = hm.SUR_SCALES.w, hm.SUR_SCALES.erho
+    e_ref = y[:, 0] * sw + y[:, 1] * se
+    e_sur = pr[:, 0] * sw + pr[:, 1] * se
+    err = float(np.linalg.norm(e_sur - e_ref) / np.linalg.norm(e_ref))
+    print(json.dumps({"workload": "surrogate-train-65536x20-batch19440", "steps": args.train_steps,
+                      "train_s": round(dt, 3), "us_per_step": round(dt / args.train_steps * 1e6, 2),
+                      "final_loss": loss, "field_rel_error": round(err, 5), "bound": 1e-2}))
+
+
 def run_mcp_vs_det(args):
     """Sec. 2, Fig. 1 at scale: the Monte Carlo plasticity against the deterministic
     multi-slip model (FP64, pseudo-inverse of the active constraints).  (1) Speed:
@@ -1001,7 +1038,7 @@ def main():
         {"2d": run_2d, "3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
          "sweep3d": run_sweep3d, "texture2d": run_texture, "texture3d": run_texture,
          "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq, "aniso": run_aniso,
-         "mcp-vs-det": run_mcp_vs_det}[args.workload](args)
+         "mcp-vs-det": run_mcp_vs_det, "surrogate-train": run_surrogate_train}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
