@@ -89,7 +89,9 @@ __global__ void k_wait_probe(long long limit, int late) {
 
 // One window (tile `tile` of plane 2 zidx + a.zpar) of one lattice; maps NULL
 // when no window of this launch is copied by TMA boxes.
-template <int WY, int FIELD, bool HASMP>
+// KEYED: the Philox round keys come from a.rk (launch parameters); otherwise
+// every thread steps the key from a.seed.
+template <int WY, int FIELD, bool HASMP, bool KEYED>
 __device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* maps, const int tile, const int zidx,
                                           unsigned char* raw) {
     using Cfg = LeanCfg<WY, HASMP>;
@@ -167,23 +169,40 @@ __device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* ma
 
     // ---- every draw of the launch, while the copies land -------------------
     // site m of phase p for this thread: colour sub-grid column = lane, row
-    // j = warp + NW m; window column 2 lane + (p & 1), row 2 j + (p >> 1)
+    // j = warp + NW m; window column 2 lane + (p & 1), row 2 j + (p >> 1).  Its
+    // Philox unit gx + Lx (gy + Ly z) is a row base plus a column, each wrapped
+    // once per thread.  Whether the row lies in the phase's region is the same
+    // for the whole warp (a branch); whether the column does is a select, so a
+    // warp never diverges here (the few edge lanes draw and drop the result).
     const uint32_t cz = 4u * (uint32_t)a.zpar;
+    const uint64_t gxc[2] = {(uint64_t)gx_of(2 * lane), (uint64_t)gx_of(2 * lane + 1)};
+    uint64_t rowb[PER][2];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int j = warp + NW * m;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            rowb[m][r] = j < Cfg::SY ? (uint64_t)a.Lx * ((uint64_t)gy_of(2 * j + r) + (uint64_t)a.Ly * (uint64_t)z) : 0;
+    }
     uint32_t u1[4][PER];
     uint32_t kk[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         kk[p] = 0;
-        const int x = 2 * lane + (p & 1), lo = p + 1, hi = WX - p - 1, loy = Cfg::ylo(p);
+        const int x = 2 * lane + (p & 1), loy = Cfg::ylo(p);
+        const bool colok = x >= p + 1 && x < WX - p - 1;
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const int j = warp + NW * m, y = 2 * j + (p >> 1);
             u1[p][m] = 0;
-            if (j < Cfg::SY && x >= lo && x < hi && y >= loy && y < WY - loy) {
-                const uint64_t unit = (uint64_t)gx_of(x) + (uint64_t)a.Lx * ((uint64_t)gy_of(y) + (uint64_t)a.Ly * z);
-                const uint4 u = draw(a.seed, unit, a.sweep, kTagSweep, cz + (uint32_t)p);
+            if (j < Cfg::SY && y >= loy && y < WY - loy) {
+                const uint64_t unit = rowb[m][p >> 1] + gxc[p & 1];
+                const uint4 u =
+                    KEYED ? philox10_keyed(a.rk, make_uint4((uint32_t)unit, (uint32_t)(unit >> 32), a.sweep,
+                                                            (kTagSweep << 24) | (cz + (uint32_t)p)))
+                          : draw(a.seed, unit, a.sweep, kTagSweep, cz + (uint32_t)p);
                 u1[p][m] = u.y;
-                kk[p] |= (__umulhi(u.x, 26u) + 1u) << (8 * m);  // 0 marks "no site"
+                kk[p] |= (colok ? __umulhi(u.x, 26u) + 1u : 0u) << (8 * m);  // 0 marks "no site"
             }
         }
     }
@@ -202,22 +221,29 @@ __device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* ma
     }
 
     const unsigned lt = (1u << lane) - 1u;
+    // kernel parameters of the test stage, once
+    const int32_t* __restrict__ ftab = a.table;
+    const uint32_t ftab_n = a.table_n;
+    const uint32_t* __restrict__ thr = a.thr;
+    const int32_t Jc = a.J, Dmax = a.D;
+    constexpr int SAFE = (WY / 2) * WX + WX / 2;  // a window position whose 26 neighbours all lie in the window
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        // ---- propose: the k-th neighbour's grain; queue those of another grain
-        uint32_t e[PER] = {};
+        // ---- propose: the k-th neighbour's grain; queue those of another grain.
+        // An empty slot (kc = 0) reads at SAFE instead, so every lane loads and
+        // no branch is taken.
+        uint32_t e[PER];
         unsigned bal[PER];
         int tot = 0;
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
             const uint32_t kc = (kk[p] >> (8 * m)) & 255u;
             const int pos = (2 * (warp + NW * m) + (p >> 1)) * WX + 2 * lane + (p & 1);
-            bool pr = false;
-            if (kc) {
-                const int k = (int)kc - 1;
-                pr = Q[pos + off[k]] != Q[pos];
-                e[m] = (uint32_t)pos | ((uint32_t)k << 16);
-            }
+            const int k = kc ? (int)kc - 1 : 0;
+            const int pq = kc ? pos : SAFE;
+            const int32_t qa = Q[pq + off[k]], qb = Q[pq];
+            const bool pr = (kc != 0u) & (qa != qb);
+            e[m] = (uint32_t)pos | ((uint32_t)k << 16);
             bal[m] = __ballot_sync(0xFFFFFFFFu, pr);
             tot += __popc(bal[m]);
         }
@@ -241,8 +267,8 @@ __device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* ma
             const int32_t qi = c[0], qj = c[o];
             int32_t mpj = 0, bi = 0, bj = 0;
             if (HASMP) mpj = MP[pos + o];
-            if (FIELD == 1) { bi = tab(a.table, a.table_n, qi); bj = tab(a.table, a.table_n, qj); }
-            if (FIELD == 2) { bi = tab(a.table, a.table_n, MP[pos]); bj = tab(a.table, a.table_n, mpj); }
+            if (FIELD == 1) { bi = tab(ftab, ftab_n, qi); bj = tab(ftab, ftab_n, qj); }
+            if (FIELD == 2) { bi = tab(ftab, ftab_n, MP[pos]); bj = tab(ftab, ftab_n, mpj); }
             int so = 0, sn = 0;
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz)
@@ -261,8 +287,8 @@ __device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* ma
                     sn += (v0 == qj) + (v2 == qj);
                     if (dz != 0 || dy != 0) { so += v1 == qi; sn += v1 == qj; }
                 }
-            const int32_t d = a.J * (so - sn) + (bj - bi);
-            if (metropolis(d, a.D, a.thr, w.y)) {
+            const int32_t d = Jc * (so - sn) + (bj - bi);
+            if (metropolis(d, Dmax, thr, w.y)) {
                 Q[pos] = qj;
                 if (HASMP) MP[pos] = mpj;
             }
@@ -298,7 +324,7 @@ template <int WY, int FIELD, bool HASMP>
 __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, LeanCfg<WY, HASMP>::MINB)
     k_lean26(const __grid_constant__ PlaneArgs a, const __grid_constant__ LeanMaps maps) {
     extern __shared__ __align__(16) unsigned char raw[];
-    lean_body<WY, FIELD, HASMP>(a, &maps, (int)blockIdx.x, (int)blockIdx.y, raw);
+    lean_body<WY, FIELD, HASMP, true>(a, &maps, (int)blockIdx.x, (int)blockIdx.y, raw);
 }
 
 // Many independent lattices in one launch: block b belongs to the replica r
@@ -324,7 +350,7 @@ __global__ void __launch_bounds__(LeanCfg<WY, HASMP>::kLT, HASMP ? 3 : 4)
         s_tile = (int)(local - (int64_t)s_zidx * sa.tiles);
     }
     __syncthreads();
-    lean_body<WY, FIELD, HASMP>(sa, nullptr, s_tile, s_zidx, raw);
+    lean_body<WY, FIELD, HASMP, false>(sa, nullptr, s_tile, s_zidx, raw);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 map_encoder() {

@@ -643,6 +643,7 @@ PlaneArgs plane_args(const hp_handle* h, int variant, const int32_t* q_in, const
     a.D = h->D;
     a.J = h->desc.J_fix;
     a.seed = h->desc.seed;
+    philox_round_keys(a.seed, a.rk);
     a.sweep = sweep;
     a.Lx = (int)h->lat.L[0];
     a.Ly = (int)h->lat.L[1];

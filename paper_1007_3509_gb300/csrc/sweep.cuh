@@ -29,6 +29,7 @@ struct PlaneArgs {
     int tiles;              // tiles per plane
     int fast;               // 1: window narrower than the lattice (wrap by one add)
     int vec;                // 1: fast and Lx % 4 == 0 (16-byte row chunks)
+    uint32_t rk[20];        // Philox round keys of seed (philox_round_keys)
 };
 
 namespace {
