@@ -86,3 +86,31 @@ def test_aniso_angles_from_orientations_and_frozen_boundary(oracle):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(q.cpu().numpy(), ref_q)
     lat.close()
+
+
+def test_aniso_at_the_bench_size_bit_exact(oracle):
+    """The anisotropic workload's lattice (1024^2 Moore, 625 grains rotated about
+    z, Read-Shockley energy and mobility, kT 0.6) for 6 MCS against the oracle,
+    site for site."""
+    torch, hm = need_gpu()
+    L, G, N = (1024, 1024), 625, 1024 * 1024
+    lat = hm.Lattice(2, L, 8, 256, 1001, G, hm.FIELD_NONE)
+    q = torch.empty(N, dtype=torch.int32, device="cuda")
+    lat.hp_bind(q)
+    ang = torch.empty(G, device="cuda")
+    lat.hp_init_voronoi(hm.ORIENT_ANGLE, ang)
+    units = torch.empty(G, dtype=torch.int32, device="cuda")
+    hm.hp_angle_units(G, hm.ORIENT_ANGLE, ang, 1000, PERIOD, units)
+    J, m = hm.hp_build_read_shockley(1.0, 15.0, 250, 181, 1000, mobility=True)
+    torch.cuda.synchronize()
+    q0 = q.cpu().numpy()
+    a = units.cpu().numpy()
+    thr, D = oracle.threshold_table(0.6)
+    lat.hp_set_threshold_table(*hm.hp_build_threshold_table(0.6))
+    lat.hp_set_anisotropy(units, PERIOD, 250, J, m)
+    lat.hp_sweep(6)
+    torch.cuda.synchronize()
+    ref_q, _, _, _ = oracle.sweep_aniso(2, L, 8, 1001, 0, 6, thr, D, q0, a, PERIOD, 250, J, m)
+    np.testing.assert_array_equal(q.cpu().numpy(), ref_q)
+    assert np.count_nonzero(ref_q != q0) > 1000
+    lat.close()

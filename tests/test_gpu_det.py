@@ -216,3 +216,36 @@ def test_fig1_monte_carlo_follows_the_deterministic_model_over_orientations(orac
             continue
         worst.append(np.abs(np.convolve(rel[first:, i], np.ones(100) / 100, mode="valid")).max())
     assert np.quantile(worst, 0.95) <= 0.035 and max(worst) <= 0.05, (np.quantile(worst, 0.95), max(worst))
+
+
+def test_det_at_the_bench_size_sampled():
+    """The speed configuration of the comparison workload: 10^6 points of random
+    orientation, 20 increments of 1e-4 in one launch; 48 sampled points against
+    the oracle to 1e-9 and every point's active set settled."""
+    torch, hm = need_gpu()
+    from oracle import svdcp
+    P, e, n = 1_000_000, 1e-4, 20
+    quat = _quats(P, 2024)
+    grain = torch.arange(P, dtype=torch.int32, device="cuda")
+    tq = torch.from_numpy(quat).cuda()
+    ep, gm = _state(torch, P)
+    sig = torch.empty(6 * P, dtype=torch.float64, device="cuda")
+    na = torch.empty(P, dtype=torch.int32, device="cuda")
+    hm.hp_det_step(_prm(hm, e), grain, tq, 0, n, ep, gm, sigma=sig, n_active=na)
+    torch.cuda.synchronize()
+    act = na.cpu().numpy()
+    assert act.min() >= 0 and (act >= 2).mean() > 0.5
+    p = dict(T1)
+    C = svdcp.stiffness(p["C11"], p["C12"], p["C44"])
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(P, size=48, replace=False))
+    s = sig.view(6, P)[:, torch.from_numpy(idx).cuda()].cpu().numpy().T
+    g = gm[torch.from_numpy(idx).cuda()].cpu().numpy()
+    for k, i in enumerate(idx):
+        R = _R(quat[i])
+        U = R.T @ np.diag([1.0, -0.5, -0.5]) @ R
+        epo, go = np.zeros((3, 3)), 0.0
+        for t in range(1, n + 1):
+            epo, go, so, _, _ = svdcp.step(p, C, t * e * U, epo, go)
+        assert np.abs(_t(s[k]) - so).max() <= 1e-9 * np.abs(so).max(), i
+        assert abs(g[k] - go) <= 1e-9 * max(go, 1e-12)
