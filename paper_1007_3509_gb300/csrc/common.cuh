@@ -160,5 +160,14 @@ int mlp_train_begin(const float* params, int64_t rows, MlpTrain* t, cudaStream_t
 // *loss (device, may be null) receives the batch loss
 int mlp_train_step(MlpTrain* t, float* params, float* m, float* v, const float* X, const float* Y, int32_t step,
                    float lr, float beta1, float beta2, float eps, float* loss, cudaStream_t s);
+// The whole run in one cooperative launch (every CTA resident, grid barriers
+// between a step's gradients and its update): step s takes minibatch (s - 1) mod
+// n_batches of X, Y (t->rows rows each) and sched[3 (s - 1) ..] = (lr, 1 - beta1^t,
+// 1 - beta2^t) (device); loss_log (device float[steps], may be null) and
+// *loss_last (device, may be null) receive the batch losses.  *ran = false (and
+// nothing done) when the device cannot keep every CTA resident.
+int mlp_train_loop(MlpTrain* t, float* params, float* m, float* v, const float* X, const float* Y, int64_t n_batches,
+                   int32_t steps, const float* sched, float beta1, float beta2, float eps, float* loss_log,
+                   float* loss_last, cudaStream_t s, bool* ran);
 void mlp_train_end(MlpTrain* t, cudaStream_t s);
 }  // namespace hp

@@ -410,6 +410,8 @@ constexpr int IMG_F = 3 * HID + OUT * HID + OUT;         // floats after them
 constexpr size_t IMG_BYTES = ((size_t)IMG_BF + 4 * IMG_F + 15) / 16 * 16;
 // per-CTA gradient slot: NPARAM gradients then the CTA's share of the loss
 constexpr int PSTR = (NPARAM + 1 + 3) / 4 * 4;
+// at most this many gradient slots (CTAs of the gradient kernel, at most one per SM)
+constexpr int kMaxSlots = 160;
 static_assert(offsetof(TrainSmem, w1) == 0 && offsetof(TrainSmem, w2) == 2 * HID * INP &&
                   offsetof(TrainSmem, w3t) + 2 * HID * HID == IMG_BF,
               "the BF16 operands are one block at the start of TrainSmem");
@@ -454,10 +456,94 @@ __global__ void k_mlp_pack(const float* __restrict__ P, unsigned char* __restric
     }
 }
 
-__global__ void __launch_bounds__(NTT, 1) k_mlp_train(const unsigned char* __restrict__ img,
-                                                      const float* __restrict__ X, const float* __restrict__ T,
-                                                      int64_t M, float inv_batch, float* __restrict__ part, int* err) {
+// Arguments of the gradient kernels.  One step (k_mlp_train): the minibatch is
+// X, T (M rows), the packed weights img_in, gradients to the CTA's slot.  A whole
+// training run (k_mlp_train_loop, a cooperative launch with every CTA resident):
+// step s = 1..steps takes minibatch (s - 1) mod n_batches (rows (s - 1 mod
+// n_batches) M .. + M of X, T), reads the packed weights from img, writes its
+// slot; after a grid barrier each CTA reduces its share of the entries over all
+// slots, applies Adam (sched[3(s-1) ..] = lr, 1 - beta1^t, 1 - beta2^t) to P,
+// m, v and rewrites those entries of img; a second grid barrier ends the step.
+struct TrainArgs {
+    const unsigned char* img_in;
+    unsigned char* img;
+    const float* X;
+    const float* T;
+    int64_t M;
+    float inv_batch;
+    float* part;
+    int* err;
+    int64_t n_batches;
+    int32_t steps;
+    const float* sched;
+    float b1, b2, eps;
+    float* P;
+    float* m;
+    float* v;
+    float* loss_log;    // [steps] or null
+    float* loss_last;   // or null
+    unsigned int* bar;  // grid barrier: arrivals, generation (zeroed before launch)
+};
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): thread 0 of
+// each CTA arrives on a counter; the last to arrive resets it and advances the
+// generation the others poll.  Bounded: after `limit` cycles a waiting CTA
+// gives up (false).  Global writes before the barrier are visible after it to
+// loads that go through L2.
+__device__ bool grid_barrier(unsigned int* bar, long long limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > limit) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum of entry i over the slots written earlier in the same launch (loads
+// through L2), by the 8 consecutive lanes of a group in a fixed order; i < 0
+// adds nothing but takes part in the shuffles.
+__device__ __forceinline__ float slot_sum_cg(const float* part, int nslots, int i) {
+    const int j = threadIdx.x & 7;
+    float acc = 0.0f;
+    if (i >= 0 && i <= NPARAM) {
+        // every load of the group issued before the sum (at most kMaxSlots slots)
+        float g[kMaxSlots / 8];
+#pragma unroll
+        for (int k = 0; k < kMaxSlots / 8; ++k) {
+            const int c = j + 8 * k;
+            g[k] = c < nslots ? __ldcg(part + (size_t)c * PSTR + i) : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxSlots / 8; ++k) acc += g[k];
+    }
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+    return acc;
+}
+
+template <bool LOOP>
+__device__ __forceinline__ void train_body(const TrainArgs& a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw + ((1024 - (saddr(smem_raw) & 1023)) & 1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -465,31 +551,12 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const unsigned char* __res
     const int r = quad * 32 + lane;  // row of the tile = TMEM lane
     const int f0 = FW * hf;          // first feature of this thread
     constexpr int RL = 32 / FW;      // lanes holding each feature after a reduce-scatter
+    const int64_t M = a.M;
+    const float inv_batch = a.inv_batch;
+    float* __restrict__ part = a.part;
+    int* err = a.err;
     if (warp == 0) tmem_alloc(saddr(&S.tmem), 512);
-    if (tid == 0) {
-        mbar_init(saddr(&S.mbar));
-        S.loss = 0.0f;
-    }
-    {   // the BF16 operands are one contiguous block at the start of TrainSmem
-        const int4* src = reinterpret_cast<const int4*>(img);
-        int4* dst = reinterpret_cast<int4*>(S.w1);
-        for (int i = tid; i < IMG_BF / 16; i += NTT) dst[i] = __ldg(src + i);
-        const float* f = reinterpret_cast<const float*>(img + IMG_BF);
-        for (int i = tid; i < HID; i += NTT) {
-            S.b1[i] = f[i];
-            S.b2[i] = f[HID + i];
-            S.b3[i] = f[2 * HID + i];
-            S.gb1[i] = S.gb2[i] = S.gb3[i] = 0.0f;
-        }
-        for (int i = tid; i < OUT * HID; i += NTT) {
-            S.w4[i] = f[3 * HID + i];
-            S.gw4[i] = 0.0f;
-        }
-        if (tid < OUT) {
-            S.b4[tid] = f[3 * HID + OUT * HID + tid];
-            S.gb4[tid] = 0.0f;
-        }
-    }
+    if (tid == 0) mbar_init(saddr(&S.mbar));
     for (int i = tid; i < TILE * TILE * 2 / 16; i += NTT) reinterpret_cast<int4*>(S.dzt)[i] = make_int4(0, 0, 0, 0);
     sync_for_mma();
     const uint32_t tm = S.tmem;
@@ -497,10 +564,8 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const unsigned char* __res
     const uint32_t lb = tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)f0;
     uint32_t phase = 0;
     const int64_t ntiles = (M + TILE - 1) / TILE;
-    bool ok = true;
-    uint32_t first = 1;  // first tile of this CTA: weight-gradient accumulators start from zero
+    bool ok = true, mma_ok = true;
     float v[FW], z[FW];
-    float my_loss = 0.0f, gb4_0 = 0.0f, gb4_1 = 0.0f;
 
     auto wait_mma = [&]() -> bool {
         const bool w = mbar_wait(mbar, phase);
@@ -515,202 +580,271 @@ __global__ void __launch_bounds__(NTT, 1) k_mlp_train(const unsigned char* __res
         if (lane % RL == 0) atomicAdd(&g[f0 + lane / RL], v[0]);
     };
 
-    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int64_t row = t * TILE + r;
-        const bool valid = row < M;
-        if (hf < 2) {   // inputs 8 hf .. 8 hf + 7 of this row
-            float xr[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int f = 8 * hf + k;
-                xr[k] = (f < IN && valid) ? X[row * IN + f] : 0.0f;
+    const int32_t nsteps = LOOP ? a.steps : 1;
+    for (int32_t step = 1; step <= nsteps && ok; ++step) {
+        const int64_t r0 = LOOP ? ((int64_t)(step - 1) % a.n_batches) * M : 0;
+        const float* __restrict__ X = a.X + r0 * IN;
+        const float* __restrict__ T = a.T + r0 * OUT;
+        {   // the packed weights: the BF16 operands are one contiguous block at
+            // the start of TrainSmem (the image of a running loop is read
+            // through L2: it was rewritten in this launch)
+            const unsigned char* img = LOOP ? a.img : a.img_in;
+            const int4* src = reinterpret_cast<const int4*>(img);
+            int4* dst = reinterpret_cast<int4*>(S.w1);
+            for (int i = tid; i < IMG_BF / 16; i += NTT) dst[i] = LOOP ? __ldcg(src + i) : __ldg(src + i);
+            const float* f = reinterpret_cast<const float*>(img + IMG_BF);
+            for (int i = tid; i < HID; i += NTT) {
+                S.b1[i] = __ldcg(f + i);
+                S.b2[i] = __ldcg(f + HID + i);
+                S.b3[i] = __ldcg(f + 2 * HID + i);
+                S.gb1[i] = S.gb2[i] = S.gb3[i] = 0.0f;
             }
-            put_row_part<INP, 1>(S.x, r, hf, xr);
-            put_col_off<8, TILE>(S.xt, r, 8 * hf, xr);
+            for (int i = tid; i < OUT * HID; i += NTT) {
+                S.w4[i] = __ldcg(f + 3 * HID + i);
+                S.gw4[i] = 0.0f;
+            }
+            if (tid < OUT) {
+                S.b4[tid] = __ldcg(f + 3 * HID + OUT * HID + tid);
+                S.gb4[tid] = 0.0f;
+            }
+            if (tid == 0) S.loss = 0.0f;
         }
         sync_for_mma();
-        // ---- forward ------------------------------------------------------
-        if (tid == 0) {
-            mma(tm + CZ1, sdesc(saddr(S.x), 128, INP * 16), sdesc(saddr(S.w1), 128, INP * 16), idesc_bf16(TILE, HID), 0);
-            mma_commit(mbar);
-        }
-        if (!(ok = wait_mma())) break;
-        tmem_ldw(lb + CZ1, v);
-#pragma unroll
-        for (int k = 0; k < FW; ++k) v[k] = gelu(v[k] + S.b1[f0 + k]);
-        put_row_part<HID, FW / 8>(S.h1, r, (FW / 8) * hf, v);
-        put_col_off<FW, TILE>(S.h1t, r, f0, v);
-        sync_for_mma();
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma(tm + CZ2, sdesc(saddr(S.h1) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w2) + 256 * kk, 128, HID * 16),
-                    idesc_bf16(TILE, HID), kk > 0);
-            mma_commit(mbar);
-        }
-        if (!(ok = wait_mma())) break;
-        tmem_ldw(lb + CZ2, v);
-#pragma unroll
-        for (int k = 0; k < FW; ++k) v[k] = gelu(v[k] + S.b2[f0 + k]);
-        put_row_part<HID, FW / 8>(S.h2, r, (FW / 8) * hf, v);
-        put_col_off<FW, TILE>(S.h2t, r, f0, v);
-        sync_for_mma();
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma(tm + CZ3, sdesc(saddr(S.h2) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w3) + 256 * kk, 128, HID * 16),
-                    idesc_bf16(TILE, HID), kk > 0);
-            mma_commit(mbar);
-        }
-        if (!(ok = wait_mma())) break;
-        tmem_ldw(lb + CZ3, z);
-        // ---- output layer, loss, dz3 ---------------------------------------
-        float p0 = 0.0f, p1 = 0.0f;  // this half's share of y
-#pragma unroll
-        for (int k = 0; k < FW; ++k) {
-            z[k] += S.b3[f0 + k];
-            v[k] = bf16r(gelu(z[k]));  // h3
-            p0 = fmaf(v[k], S.w4[f0 + k], p0);
-            p1 = fmaf(v[k], S.w4[HID + f0 + k], p1);
-        }
-        S.yp[hf][r] = make_float2(p0, p1);
-        __syncthreads();
-        float y0 = S.b4[0], y1 = S.b4[1];
-#pragma unroll
-        for (int h = 0; h < NH; ++h) {
-            const float2 yh = S.yp[h][r];
-            y0 += yh.x;
-            y1 += yh.y;
-        }
-        float d0 = 0.0f, d1 = 0.0f;
-        if (valid) {
-            const float e0 = y0 - T[row * OUT + 0], e1 = y1 - T[row * OUT + 1];
-            if (hf == 0) my_loss += e0 * e0 + e1 * e1;
-            d0 = e0 * inv_batch;
-            d1 = e1 * inv_batch;
-        }
-        if (hf == 0) {
-            gb4_0 += d0;
-            gb4_1 += d1;
-        }
-        {   // dW4[o][k] = sum_rows d_o h3_k
-            float g[FW];
-#pragma unroll
-            for (int k = 0; k < FW; ++k) g[k] = d0 * v[k];
-            warp_reduce_scatter<FW>(g);
-            if (lane % RL == 0) atomicAdd(&S.gw4[f0 + lane / RL], g[0]);
-#pragma unroll
-            for (int k = 0; k < FW; ++k) g[k] = d1 * v[k];
-            warp_reduce_scatter<FW>(g);
-            if (lane % RL == 0) atomicAdd(&S.gw4[HID + f0 + lane / RL], g[0]);
-        }
-#pragma unroll
-        for (int k = 0; k < FW; ++k)
-            v[k] = (d0 * S.w4[f0 + k] + d1 * S.w4[HID + f0 + k]) * gelu_grad(z[k]);  // dz3
-        put_row_part<HID, FW / 8>(S.dz, r, (FW / 8) * hf, v);
-        put_col_off<FW, TILE>(S.dzt, r, f0, v);
-        bias_grad(S.gb3);
-        sync_for_mma();
-        // ---- dh2 = dz3 W3, dW3 += dz3^T h2 ---------------------------------
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma(tm + CDH, sdesc(saddr(S.dz) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w3t) + 256 * kk, 128, HID * 16),
-                    idesc_bf16(TILE, HID), kk > 0);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-                mma(tm + CDW3, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.h2t) + 256 * kk, 128, TILE * 16),
-                    idesc_bf16(TILE, HID), (kk > 0) | (first ^ 1));
-            mma_commit(mbar);
-        }
-        if (!(ok = wait_mma())) break;
-        tmem_ldw(lb + CDH, v);
-        tmem_ldw(lb + CZ2, z);
-#pragma unroll
-        for (int k = 0; k < FW; ++k) v[k] *= gelu_grad(z[k] + S.b2[f0 + k]);  // dz2
-        put_row_part<HID, FW / 8>(S.dz, r, (FW / 8) * hf, v);
-        put_col_off<FW, TILE>(S.dzt, r, f0, v);
-        bias_grad(S.gb2);
-        sync_for_mma();
-        // ---- dh1 = dz2 W2, dW2 += dz2^T h1 ---------------------------------
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma(tm + CDH, sdesc(saddr(S.dz) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w2t) + 256 * kk, 128, HID * 16),
-                    idesc_bf16(TILE, HID), kk > 0);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-                mma(tm + CDW2, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.h1t) + 256 * kk, 128, TILE * 16),
-                    idesc_bf16(TILE, HID), (kk > 0) | (first ^ 1));
-            mma_commit(mbar);
-        }
-        if (!(ok = wait_mma())) break;
-        tmem_ldw(lb + CDH, v);
-        tmem_ldw(lb + CZ1, z);
-#pragma unroll
-        for (int k = 0; k < FW; ++k) v[k] *= gelu_grad(z[k] + S.b1[f0 + k]);  // dz1
-        put_col_off<FW, TILE>(S.dzt, r, f0, v);
-        bias_grad(S.gb1);
-        sync_for_mma();
-        // ---- dW1 += dz1^T x -------------------------------------------------
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk)
-                mma(tm + CDW1, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.xt) + 256 * kk, 128, TILE * 16),
-                    idesc_bf16(TILE, INP), (kk > 0) | (first ^ 1));
-            mma_commit(mbar);
-        }
-        if (!(ok = wait_mma())) break;
-        first = 0;
-    }
-    // ---- this CTA's gradients to its slot (plain stores; every entry written) --
-    if (ok && !first) {
-        float* slot = part + (size_t)blockIdx.x * PSTR;
-        // weight gradients: TMEM lanes 0..63 (quadrants 0 and 1) hold dW rows
-        // (out features); each group of four warps takes FW of the columns
-        if (quad < 2) {
-            const int o = r;  // out feature
-            tmem_ldw(lb + CDW3, v);
-#pragma unroll
-            for (int k = 0; k < FW; k += 4)
-                *reinterpret_cast<float4*>(slot + OW3 + o * HID + f0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
-            tmem_ldw(lb + CDW2, v);
-#pragma unroll
-            for (int k = 0; k < FW; k += 4)
-                *reinterpret_cast<float4*>(slot + OW2 + o * HID + f0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+        uint32_t first = 1;  // first tile of this CTA in the step: weight-gradient accumulators start from zero
+        float my_loss = 0.0f, gb4_0 = 0.0f, gb4_1 = 0.0f;
+
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t row = t * TILE + r;
+            const bool valid = row < M;
+            if (hf < 2) {   // inputs 8 hf .. 8 hf + 7 of this row
+                float xr[8];
+    #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int f = 8 * hf + k;
+                    xr[k] = (f < IN && valid) ? X[row * IN + f] : 0.0f;
+                }
+                put_row_part<INP, 1>(S.x, r, hf, xr);
+                put_col_off<8, TILE>(S.xt, r, 8 * hf, xr);
+            }
+            sync_for_mma();
+            // ---- forward ------------------------------------------------------
+            if (tid == 0) {
+                mma(tm + CZ1, sdesc(saddr(S.x), 128, INP * 16), sdesc(saddr(S.w1), 128, INP * 16), idesc_bf16(TILE, HID), 0);
+                mma_commit(mbar);
+            }
+            if (!(ok = wait_mma())) break;
+            tmem_ldw(lb + CZ1, v);
+    #pragma unroll
+            for (int k = 0; k < FW; ++k) v[k] = gelu(v[k] + S.b1[f0 + k]);
+            put_row_part<HID, FW / 8>(S.h1, r, (FW / 8) * hf, v);
+            put_col_off<FW, TILE>(S.h1t, r, f0, v);
+            sync_for_mma();
+            if (tid == 0) {
+    #pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma(tm + CZ2, sdesc(saddr(S.h1) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w2) + 256 * kk, 128, HID * 16),
+                        idesc_bf16(TILE, HID), kk > 0);
+                mma_commit(mbar);
+            }
+            if (!(ok = wait_mma())) break;
+            tmem_ldw(lb + CZ2, v);
+    #pragma unroll
+            for (int k = 0; k < FW; ++k) v[k] = gelu(v[k] + S.b2[f0 + k]);
+            put_row_part<HID, FW / 8>(S.h2, r, (FW / 8) * hf, v);
+            put_col_off<FW, TILE>(S.h2t, r, f0, v);
+            sync_for_mma();
+            if (tid == 0) {
+    #pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma(tm + CZ3, sdesc(saddr(S.h2) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w3) + 256 * kk, 128, HID * 16),
+                        idesc_bf16(TILE, HID), kk > 0);
+                mma_commit(mbar);
+            }
+            if (!(ok = wait_mma())) break;
+            tmem_ldw(lb + CZ3, z);
+            // ---- output layer, loss, dz3 ---------------------------------------
+            float p0 = 0.0f, p1 = 0.0f;  // this half's share of y
+    #pragma unroll
+            for (int k = 0; k < FW; ++k) {
+                z[k] += S.b3[f0 + k];
+                v[k] = bf16r(gelu(z[k]));  // h3
+                p0 = fmaf(v[k], S.w4[f0 + k], p0);
+                p1 = fmaf(v[k], S.w4[HID + f0 + k], p1);
+            }
+            S.yp[hf][r] = make_float2(p0, p1);
+            __syncthreads();
+            float y0 = S.b4[0], y1 = S.b4[1];
+    #pragma unroll
+            for (int h = 0; h < NH; ++h) {
+                const float2 yh = S.yp[h][r];
+                y0 += yh.x;
+                y1 += yh.y;
+            }
+            float d0 = 0.0f, d1 = 0.0f;
+            if (valid) {
+                const float e0 = y0 - T[row * OUT + 0], e1 = y1 - T[row * OUT + 1];
+                if (hf == 0) my_loss += e0 * e0 + e1 * e1;
+                d0 = e0 * inv_batch;
+                d1 = e1 * inv_batch;
+            }
             if (hf == 0) {
-                tmem_ldw(lb + CDW1, v);  // the first 16 columns hold dW1
-#pragma unroll
-                for (int k = 0; k < IN; ++k) slot[OW1 + o * IN + k] = v[k];
+                gb4_0 += d0;
+                gb4_1 += d1;
             }
+            {   // dW4[o][k] = sum_rows d_o h3_k
+                float g[FW];
+    #pragma unroll
+                for (int k = 0; k < FW; ++k) g[k] = d0 * v[k];
+                warp_reduce_scatter<FW>(g);
+                if (lane % RL == 0) atomicAdd(&S.gw4[f0 + lane / RL], g[0]);
+    #pragma unroll
+                for (int k = 0; k < FW; ++k) g[k] = d1 * v[k];
+                warp_reduce_scatter<FW>(g);
+                if (lane % RL == 0) atomicAdd(&S.gw4[HID + f0 + lane / RL], g[0]);
+            }
+    #pragma unroll
+            for (int k = 0; k < FW; ++k)
+                v[k] = (d0 * S.w4[f0 + k] + d1 * S.w4[HID + f0 + k]) * gelu_grad(z[k]);  // dz3
+            put_row_part<HID, FW / 8>(S.dz, r, (FW / 8) * hf, v);
+            put_col_off<FW, TILE>(S.dzt, r, f0, v);
+            bias_grad(S.gb3);
+            sync_for_mma();
+            // ---- dh2 = dz3 W3, dW3 += dz3^T h2 ---------------------------------
+            if (tid == 0) {
+    #pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma(tm + CDH, sdesc(saddr(S.dz) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w3t) + 256 * kk, 128, HID * 16),
+                        idesc_bf16(TILE, HID), kk > 0);
+    #pragma unroll
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tm + CDW3, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.h2t) + 256 * kk, 128, TILE * 16),
+                        idesc_bf16(TILE, HID), (kk > 0) | (first ^ 1));
+                mma_commit(mbar);
+            }
+            if (!(ok = wait_mma())) break;
+            tmem_ldw(lb + CDH, v);
+            tmem_ldw(lb + CZ2, z);
+    #pragma unroll
+            for (int k = 0; k < FW; ++k) v[k] *= gelu_grad(z[k] + S.b2[f0 + k]);  // dz2
+            put_row_part<HID, FW / 8>(S.dz, r, (FW / 8) * hf, v);
+            put_col_off<FW, TILE>(S.dzt, r, f0, v);
+            bias_grad(S.gb2);
+            sync_for_mma();
+            // ---- dh1 = dz2 W2, dW2 += dz2^T h1 ---------------------------------
+            if (tid == 0) {
+    #pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma(tm + CDH, sdesc(saddr(S.dz) + 256 * kk, 128, HID * 16), sdesc(saddr(S.w2t) + 256 * kk, 128, HID * 16),
+                        idesc_bf16(TILE, HID), kk > 0);
+    #pragma unroll
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tm + CDW2, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.h1t) + 256 * kk, 128, TILE * 16),
+                        idesc_bf16(TILE, HID), (kk > 0) | (first ^ 1));
+                mma_commit(mbar);
+            }
+            if (!(ok = wait_mma())) break;
+            tmem_ldw(lb + CDH, v);
+            tmem_ldw(lb + CZ1, z);
+    #pragma unroll
+            for (int k = 0; k < FW; ++k) v[k] *= gelu_grad(z[k] + S.b1[f0 + k]);  // dz1
+            put_col_off<FW, TILE>(S.dzt, r, f0, v);
+            bias_grad(S.gb1);
+            sync_for_mma();
+            // ---- dW1 += dz1^T x -------------------------------------------------
+            if (tid == 0) {
+    #pragma unroll
+                for (int kk = 0; kk < 8; ++kk)
+                    mma(tm + CDW1, sdesc(saddr(S.dzt) + 256 * kk, 128, TILE * 16), sdesc(saddr(S.xt) + 256 * kk, 128, TILE * 16),
+                        idesc_bf16(TILE, INP), (kk > 0) | (first ^ 1));
+                mma_commit(mbar);
+            }
+            if (!(ok = wait_mma())) break;
+            first = 0;
         }
-        // per-row reductions of the loss and b4 gradient (the other groups add zeros)
-        for (int m = 16; m >= 1; m >>= 1) {
-            my_loss += __shfl_xor_sync(0xFFFFFFFFu, my_loss, m);
-            gb4_0 += __shfl_xor_sync(0xFFFFFFFFu, gb4_0, m);
-            gb4_1 += __shfl_xor_sync(0xFFFFFFFFu, gb4_1, m);
+        // ---- this CTA's gradients to its slot (plain stores; every entry written) --
+        if (ok && !first) {
+            float* slot = part + (size_t)blockIdx.x * PSTR;
+            // weight gradients: TMEM lanes 0..63 (quadrants 0 and 1) hold dW rows
+            // (out features); each group of four warps takes FW of the columns
+            if (quad < 2) {
+                const int o = r;  // out feature
+                tmem_ldw(lb + CDW3, v);
+    #pragma unroll
+                for (int k = 0; k < FW; k += 4)
+                    *reinterpret_cast<float4*>(slot + OW3 + o * HID + f0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                tmem_ldw(lb + CDW2, v);
+    #pragma unroll
+                for (int k = 0; k < FW; k += 4)
+                    *reinterpret_cast<float4*>(slot + OW2 + o * HID + f0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                if (hf == 0) {
+                    tmem_ldw(lb + CDW1, v);  // the first 16 columns hold dW1
+    #pragma unroll
+                    for (int k = 0; k < IN; ++k) slot[OW1 + o * IN + k] = v[k];
+                }
+            }
+            // per-row reductions of the loss and b4 gradient (the other groups add zeros)
+            for (int m = 16; m >= 1; m >>= 1) {
+                my_loss += __shfl_xor_sync(0xFFFFFFFFu, my_loss, m);
+                gb4_0 += __shfl_xor_sync(0xFFFFFFFFu, gb4_0, m);
+                gb4_1 += __shfl_xor_sync(0xFFFFFFFFu, gb4_1, m);
+            }
+            if (lane == 0) {
+                atomicAdd(&S.loss, my_loss);
+                atomicAdd(&S.gb4[0], gb4_0);
+                atomicAdd(&S.gb4[1], gb4_1);
+            }
+            __syncthreads();
+            for (int i = tid; i < HID; i += NTT) {
+                slot[OB1 + i] = S.gb1[i];
+                slot[OB2 + i] = S.gb2[i];
+                slot[OB3 + i] = S.gb3[i];
+            }
+            for (int i = tid; i < OUT * HID; i += NTT) slot[OW4 + i] = S.gw4[i];
+            if (tid < OUT) slot[OB4 + tid] = S.gb4[tid];
+            if (tid == 0) slot[NPARAM] = S.loss * 0.5f * inv_batch;
         }
-        if (lane == 0) {
-            atomicAdd(&S.loss, my_loss);
-            atomicAdd(&S.gb4[0], gb4_0);
-            atomicAdd(&S.gb4[1], gb4_1);
+        mma_ok = ok;
+        if (LOOP && ok) {
+            ok = grid_barrier(a.bar, kWaitCycles);
+            if (ok) {
+                // this CTA's share of the entries: reduce over every slot, Adam, repack
+                const int nslots = (int)gridDim.x;
+                const int chunk = (NPARAM + 1 + nslots - 1) / nslots;
+                const int lo = (int)blockIdx.x * chunk, hi = min(lo + chunk, NPARAM + 1);
+                const float lr = a.sched[3 * (step - 1)], c1 = a.sched[3 * (step - 1) + 1],
+                            c2 = a.sched[3 * (step - 1) + 2];
+                for (int base = lo; base < hi; base += NTT / 8) {
+                    const int i = base + (tid >> 3);
+                    const float gi = slot_sum_cg(part, nslots, i < hi ? i : -1);
+                    if ((tid & 7) == 0 && i < hi) {
+                        if (i == NPARAM) {
+                            if (a.loss_log) a.loss_log[step - 1] = gi;
+                            if (a.loss_last) *a.loss_last = gi;
+                        } else {
+                            const float mi = a.b1 * a.m[i] + (1.0f - a.b1) * gi;
+                            const float vi = a.b2 * a.v[i] + (1.0f - a.b2) * gi * gi;
+                            a.m[i] = mi;
+                            a.v[i] = vi;
+                            const float pv = a.P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + a.eps);
+                            a.P[i] = pv;
+                            pack_param(a.img, i, pv);
+                        }
+                    }
+                }
+                ok = grid_barrier(a.bar, kWaitCycles);
+            }
+            if (!ok && tid == 0) atomicMax(err, 1);  // a barrier ran out; nothing is in flight
         }
-        __syncthreads();
-        for (int i = tid; i < HID; i += NTT) {
-            slot[OB1 + i] = S.gb1[i];
-            slot[OB2 + i] = S.gb2[i];
-            slot[OB3 + i] = S.gb3[i];
-        }
-        for (int i = tid; i < OUT * HID; i += NTT) slot[OW4 + i] = S.gw4[i];
-        if (tid < OUT) slot[OB4 + tid] = S.gb4[tid];
-        if (tid == 0) slot[NPARAM] = S.loss * 0.5f * inv_batch;
     }
-    if (!ok) drain_after_timeout(mbar, phase, err);
+    if (!mma_ok) drain_after_timeout(mbar, phase, err);
     fence_before();
     __syncthreads();
     fence_after();
     if (warp == 0) tmem_dealloc(tm, 512);
 }
+
+__global__ void __launch_bounds__(NTT, 1) k_mlp_train(const __grid_constant__ TrainArgs a) { train_body<false>(a); }
+__global__ void __launch_bounds__(NTT, 1) k_mlp_train_loop(const __grid_constant__ TrainArgs a) { train_body<true>(a); }
 
 // Adam on the FP32 master weights (bias-corrected; t counts from 1)
 __global__ void k_adam(float* __restrict__ P, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -731,8 +865,16 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ g, float
 __device__ __forceinline__ float slot_sum(const float* __restrict__ part, int nslots, int i) {
     const int j = threadIdx.x & 7;
     float acc = 0.0f;
-    if (i <= NPARAM)
-        for (int c = j; c < nslots; c += 8) acc += part[(size_t)c * PSTR + i];
+    if (i <= NPARAM) {
+        float g[kMaxSlots / 8];
+#pragma unroll
+        for (int k = 0; k < kMaxSlots / 8; ++k) {
+            const int c = j + 8 * k;
+            g[k] = c < nslots ? part[(size_t)c * PSTR + i] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxSlots / 8; ++k) acc += g[k];
+    }
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
@@ -865,6 +1007,8 @@ int train_configure() {
     if (!configured) {
         HP_CUDA(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(sizeof(TrainSmem) + 1024)));
+        HP_CUDA(cudaFuncSetAttribute(k_mlp_train_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(TrainSmem) + 1024)));
         configured = true;
     }
     return HP_OK;
@@ -872,14 +1016,25 @@ int train_configure() {
 
 int64_t train_grid(int64_t M) {
     const int64_t tiles = (M + TILE - 1) / TILE;
-    return tiles < sm_count() ? tiles : sm_count();
+    int64_t g = tiles < sm_count() ? tiles : sm_count();
+    return g < kMaxSlots ? g : kMaxSlots;
 }
 
 int launch_train(const unsigned char* img, const float* X, const float* T, int64_t M, float* part, int* err,
                  cudaStream_t s) {
+    TrainArgs a;
+    memset(&a, 0, sizeof(a));
+    a.img_in = img;
+    a.X = X;
+    a.T = T;
+    a.M = M;
+    a.inv_batch = 1.0f / (float)M;
+    a.part = part;
+    a.err = err;
+    a.n_batches = 1;
+    a.steps = 1;
     ::hp::count_launch();
-    k_mlp_train<<<(unsigned)train_grid(M), NTT, sizeof(TrainSmem) + 1024, s>>>(img, X, T, M, 1.0f / (float)M, part,
-                                                                              err);
+    k_mlp_train<<<(unsigned)train_grid(M), NTT, sizeof(TrainSmem) + 1024, s>>>(a);
     HP_LAUNCH_CHECK("k_mlp_train");
     return HP_OK;
 }
@@ -919,6 +1074,59 @@ int mlp_train_step(MlpTrain* t, float* params, float* m, float* v, const float* 
     k_mlp_reduce_adam<<<kRedBlocks, kRedT, 0, s>>>(t->part, (int)t->grid, params, m, v, t->img, loss, lr, beta1, beta2,
                                                    eps, c1, c2);
     HP_LAUNCH_CHECK("k_mlp_reduce_adam");
+    return HP_OK;
+}
+
+int mlp_train_loop(MlpTrain* t, float* params, float* m, float* v, const float* X, const float* Y, int64_t n_batches,
+                   int32_t steps, const float* sched, float beta1, float beta2, float eps, float* loss_log,
+                   float* loss_last, cudaStream_t s, bool* ran) {
+    *ran = false;
+    if (!t || !t->img || !t->part || steps < 1 || n_batches < 1)
+        return set_error(HP_ERR_ARG, "mlp_train_loop: bad arguments");
+    int dev = 0, coop = 0, per_sm = 0;
+    HP_CUDA(cudaGetDevice(&dev));
+    HP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    HP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_train_loop, NTT, sizeof(TrainSmem) + 1024));
+    if (!coop || (int64_t)per_sm * sm_count() < t->grid) return HP_OK;  // every CTA must be resident
+    int* err = nullptr;
+    int rc = error_flag(&err);
+    if (rc) return rc;
+    unsigned int* bar = nullptr;
+    if (cudaMallocAsync((void**)&bar, 2 * sizeof(unsigned int), s) != cudaSuccess)
+        return set_error(HP_ERR_OOM, "mlp_train_loop: allocation failed");
+    HP_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+    TrainArgs a;
+    memset(&a, 0, sizeof(a));
+    a.img = t->img;
+    a.X = X;
+    a.T = Y;
+    a.M = t->rows;
+    a.inv_batch = 1.0f / (float)t->rows;
+    a.part = t->part;
+    a.err = err;
+    a.n_batches = n_batches;
+    a.steps = steps;
+    a.sched = sched;
+    a.b1 = beta1;
+    a.b2 = beta2;
+    a.eps = eps;
+    a.P = params;
+    a.m = m;
+    a.v = v;
+    a.loss_log = loss_log;
+    a.loss_last = loss_last;
+    a.bar = bar;
+    void* args[] = {&a};
+    ::hp::count_launch();
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_mlp_train_loop, dim3((unsigned)t->grid), dim3(NTT),
+                                                      args, sizeof(TrainSmem) + 1024, s);
+    cudaFreeAsync(bar, s);
+    if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+        cudaGetLastError();  // refused before any work: the caller steps instead
+        return HP_OK;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "k_mlp_train_loop");
+    *ran = true;
     return HP_OK;
 }
 
