@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--edge", type=int, default=None,
                    help="3D workloads: lattice edge (default 1024, or 512 for 3d-cp); grains scale with the volume")
     p.add_argument("--workload", choices=["3d", "2d", "3d-cp", "ensemble", "surrogate", "sweep3d", "texture2d",
-                                          "texture3d", "texture-seeds", "3d-eq", "aniso", "mcp-vs-det", "surrogate-train"],
+                                          "texture3d", "texture-seeds", "3d-eq", "aniso", "mcp-vs-det", "surrogate-train", "small2d"],
                    default="3d",
                    help="3d: 1024^3 plasticity-driven hybrid (default line); 2d: 4096^2 Moore; 3d-cp: 512^3 "
                         "plasticity-driven whole job; ensemble: 256 replicas; surrogate: 1024^3 plain vs surrogate "
@@ -69,7 +69,7 @@ def parse():
     if a.mcs is None:
         a.mcs = {"3d": 50, "2d": W.n_mcs, "3d-cp": 500, "ensemble": 200, "surrogate": 500, "sweep3d": 20,
                  "texture2d": 1000, "texture3d": 400, "texture-seeds": 500, "3d-eq": 500, "aniso": 200,
-                 "mcp-vs-det": 0, "surrogate-train": 0}[a.workload]
+                 "mcp-vs-det": 0, "surrogate-train": 0, "small2d": 100}[a.workload]
     return a
 
 
@@ -909,6 +909,76 @@ def run_aniso(args):
     print(json.dumps({"workload": "aniso-2d-1024-moore8-g625-read-shockley", "mcs": args.mcs, "kT": 0.6, **out}))
 
 
+def run_small2d(args):
+    """The small 2D workload: 128^2, 4 neighbours (red/black), 64 Voronoi grains
+    with one angle each, per-grain stored energy U[0, 0.1] J in fixed point, J = 1,
+    kT 0.5, 100 MCS per step.  A 64 KB lattice, so launch- and latency-bound:
+    site-updates/s with the sweep's kernel launches issued per call (hp_sweep)
+    against one CUDA-graph replay per step (a one-lattice hp_ensemble); both
+    lattices must agree site for site.  The oracle's time for the same job is the
+    CPU baseline."""
+    import torch
+    from paper_1007_3509_gb300 import build, hmcpotts as hm
+    build.build()
+    torch.cuda.set_device(0)
+    Wk = synth.W2D_SMALL
+    N = Wk.N
+    b_grain = np.rint(256.0 * synth.uniform_energies(Wk.G, 0.1, Wk.seed + 1)).astype(np.int32)
+    thr, D = hm.hp_build_threshold_table(Wk.kT)
+
+    def make():
+        lat = hm.Lattice(2, Wk.L, 4, 256, Wk.seed, Wk.G, hm.FIELD_GRAIN)
+        q = torch.empty(N, dtype=torch.int32, device="cuda")
+        lat.hp_bind(q)
+        ang = torch.empty(Wk.G, device="cuda")
+        lat.hp_init_voronoi(hm.ORIENT_ANGLE, ang)
+        b = torch.from_numpy(b_grain).cuda()
+        lat.hp_set_field(b)
+        lat.hp_set_threshold_table(thr, D)
+        return lat, q, b
+
+    lat, q, b = make()
+    q0 = q.cpu().numpy()
+    glat, gq, gb = make()
+    ens = hm.Ensemble([glat])
+    # each path runs the tile variant its own autotuner picks (state restored)
+    v_launch, _ = lat.hp_sweep_autotune(2)
+    v_graph, _ = ens.hp_ensemble_autotune(2)
+    out = {"variant_launches": int(v_launch), "variant_graph": int(v_graph)}
+    for name, run in (("launches", lambda: lat.hp_sweep(args.mcs)), ("graph", lambda: ens.hp_ensemble_sweep(args.mcs))):
+        times = []
+        for rep in range(args.warmup + args.steps):
+            e0, e1 = _events(torch)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(times)
+        out[name] = {"site_updates_per_s": round(N * args.mcs / t, 1), "us_per_mcs": round(t / args.mcs * 1e6, 2)}
+    same = bool(torch.equal(q, gq))
+    import oracle
+    othr, oD = oracle.threshold_table(Wk.kT)
+    t0 = time.perf_counter()
+    ref, _, _, _ = oracle.sweep(2, Wk.L, 4, 256, Wk.seed, 0, args.mcs, othr, oD, q0, b_grain[q0])
+    cpu_s = time.perf_counter() - t0
+    # the GPU lattice after its first step equals the oracle's after the same MCS
+    lat2, q2, b2 = make()
+    lat2.hp_sweep(args.mcs)
+    torch.cuda.synchronize()
+    exact = bool(np.array_equal(q2.cpu().numpy(), ref))
+    print(json.dumps({"workload": Wk.name, "lattice": list(Wk.L), "nbr": 4, "grains": Wk.G, "kT": Wk.kT,
+                      "mcs_per_step": args.mcs, "steps": args.steps, "warmup": args.warmup, **out,
+                      "graph_over_launches": round(out["graph"]["site_updates_per_s"] /
+                                                   out["launches"]["site_updates_per_s"], 3),
+                      "graph_and_launches_agree": same, "bit_exact_vs_oracle_first_step": exact,
+                      "cpu_baseline": {"value": round(N * args.mcs / cpu_s, 1), "unit": "site-updates/s",
+                                       "kind": "oracle", "cores": 1, "sample": f"the same {args.mcs} MCS"}}))
+    for l in (lat, glat, lat2):
+        l.close()
+
+
 def run_surrogate_train(args):
     """The surrogate's training on its own: 65536 orientations x 20 load steps of
     plasticity samples (128 histories each), Adam on 972-orientation minibatches
@@ -1052,7 +1122,8 @@ def main():
         {"2d": run_2d, "3d-cp": run_3d_cp, "ensemble": run_ensemble, "surrogate": run_surrogate,
          "sweep3d": run_sweep3d, "texture2d": run_texture, "texture3d": run_texture,
          "texture-seeds": run_texture_seeds, "3d-eq": run_3d_eq, "aniso": run_aniso,
-         "mcp-vs-det": run_mcp_vs_det, "surrogate-train": run_surrogate_train}[args.workload](args)
+         "mcp-vs-det": run_mcp_vs_det, "surrogate-train": run_surrogate_train,
+         "small2d": run_small2d}[args.workload](args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
