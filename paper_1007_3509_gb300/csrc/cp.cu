@@ -195,18 +195,37 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         if (!hard) {
             xs = (at - g0) / k;
         } else {
-            // Newton on the FP64 residual; the step uses an FP32 reciprocal of
-            // the slope (a relative step error near 1e-7 leaves the iteration
-            // converging to the same FP64 root, tested on the exact residual)
+            // residual f(x) = (|tau| - g0) - k x - sat (1 - exp(-hr x)), sat = taus - g0.
+            // For y = hr x small the exponential is its cubic Taylor polynomial to
+            // 1e-12 relative (y <= 1e-2), so x solves x = (a0 + c2 x^2 - c3 x^3) / K
+            // with K = k + sat hr, c2 = sat hr^2 / 2, c3 = sat hr^3 / 6; each
+            // fixed-point step gains a factor y / 2, and three steps from x = a0 / K
+            // leave a relative error near 1e-11.  1 / K: an FP32 reciprocal with
+            // one FP64 Newton correction (relative error near 1e-14).
             const double sat = a.taus - g0;
-            xs = (at - g0) * (double)(1.0f / (float)(k + sat * hr));
+            const double K = k + sat * hr;
+            double rK = (double)(1.0f / (float)K);
+            rK = rK * (2.0 - K * rK);
+            const double a0 = at - g0;
+            xs = a0 * rK;
+            if (hr * xs <= 1e-2) {
+                const double c2 = 0.5 * sat * hr * hr * rK, c3 = (1.0 / 6.0) * sat * hr * hr * hr * rK;
+                const double x1 = xs;
+#pragma unroll
+                for (int it = 0; it < 3; ++it) xs = x1 + xs * xs * (c2 - c3 * xs);
+            } else {
+                // larger slips: Newton on the FP64 residual; the step uses an FP32
+                // reciprocal of the slope (a relative step error near 1e-7 leaves
+                // the iteration converging to the same FP64 root, tested on the
+                // exact residual)
 #pragma unroll 1
-            for (int it = 0; it < 8; ++it) {
-                const double ey = exp_neg(hr * xs);
-                const double f = at - xs * k - (a.taus - sat * ey);
-                if (fabs(f) < 1e-13 * a.tau0) break;
-                const double fp = -k - sat * hr * ey;
-                xs -= f * (double)(1.0f / (float)fp);
+                for (int it = 0; it < 8; ++it) {
+                    const double ey = exp_neg(hr * xs);
+                    const double f = at - xs * k - (a.taus - sat * ey);
+                    if (fabs(f) < 1e-13 * a.tau0) break;
+                    const double fp = -k - sat * hr * ey;
+                    xs -= f * (double)(1.0f / (float)fp);
+                }
             }
         }
         const float sg = tau_pick > 0.f ? 1.f : -1.f;
