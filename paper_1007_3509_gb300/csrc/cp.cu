@@ -11,7 +11,9 @@
 //   (E_a = 1/2 ee_a : C : ee_a with ee_a = ee - x sign(tau_a) P_a).  For the
 //   selection the candidates use the first Newton iterate from x = 0 in FP32
 //   (relative error ~1e-6 for load steps of 1e-4); the chosen system's map is
-//   then solved to convergence by Newton in FP64 and committed;
+//   then solved in FP64 (for hr x <= 1e-2 three fixed-point steps on the cubic
+//   Taylor form of the Voce term, relative error ~1e-10; Newton otherwise) and
+//   committed, the new resistance from consistency, g = |tau| - k x;
 //   p_a = exp(-beta (dE_a - min dE)) / Z (Eq. (1)); R = u0 / 2^32 from
 //   Philox(seed; p, t, tag 1); first a with R < sum_{b<=a} p_b (Eq. (2)),
 //   all in FP32 (FP64 is kept for the return map alone);
@@ -122,6 +124,8 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
     const double dtau = a.taus - a.tau0;
     const bool hard = dtau > 0.0 && a.h0 > 0.0;
     const double hr = hard ? a.h0 / dtau : 0.0;
+    const float hr32 = (float)hr, taus32 = (float)a.taus;
+    const double hr2h = 0.5 * hr * hr, hr3s = hr * hr * hr / 6.0;  // series coefficients of 1 - exp(-hr x)
     float ee[6], s[6];
     for (int32_t inc = 1; inc <= a.n_incr; ++inc) {
         const uint32_t t = a.t0 + (uint32_t)inc;
@@ -144,8 +148,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         // candidate energies for the selection (Eq. (1)): the linearised
         // return map x_a = (|tau_a| - g)/(k_a + dg/dgamma), relative error
         // about 1e-6 against the converged one, in FP32
-        const float sat32 = (float)(a.taus - (double)gres);
-        const float hg = hard ? sat32 * (float)hr : 0.0f;
+        const float hg = hard ? (taus32 - gres) * hr32 : 0.0f;
         float dE[12];
         float dEmin = 3.4e38f;
 #pragma unroll
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
             const double a0 = at - g0;
             xs = a0 * rK;
             if (hr * xs <= 1e-2) {
-                const double c2 = 0.5 * sat * hr * hr * rK, c3 = (1.0 / 6.0) * sat * hr * hr * hr * rK;
+                const double sr = sat * rK, c2 = hr2h * sr, c3 = hr3s * sr;
                 const double x1 = xs;
 #pragma unroll
                 for (int it = 0; it < 3; ++it) xs = x1 + xs * xs * (c2 - c3 * xs);
@@ -239,7 +242,8 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         ep[4] += xf * 0.5f * (m0 * n2 + m2 * n0);
         ep[5] += xf * 0.5f * (m0 * n1 + m1 * n0);
         gam += (float)xs;
-        gres = hard ? (float)(a.taus - (a.taus - g0) * exp_neg(hr * xs)) : gres;
+        // consistency at the solved slip: g(gamma + x) = |tau| - k x
+        gres = hard ? (float)(at - k * xs) : gres;
     }
 #pragma unroll
     for (int v = 0; v < 6; ++v) a.eps_p[(int64_t)v * a.P + p] = ep[v];
