@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
     const bool hard = dtau > 0.0 && a.h0 > 0.0;
     const double hr = hard ? a.h0 / dtau : 0.0;
     const float hr32 = (float)hr, taus32 = (float)a.taus;
-    const double hr2h = 0.5 * hr * hr, hr3s = hr * hr * hr / 6.0;  // series coefficients of 1 - exp(-hr x)
+    // series coefficients of 1 - exp(-hr x) = hr x - (hr x)^2 / 2 + (hr x)^3 / 6 - ...
+    const float hr2h = (float)(0.5 * hr * hr), hr3s = (float)(hr * hr * hr / 6.0);
     float ee[6], s[6];
     for (int32_t inc = 1; inc <= a.n_incr; ++inc) {
         const uint32_t t = a.t0 + (uint32_t)inc;
@@ -201,21 +202,29 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
             // residual f(x) = (|tau| - g0) - k x - sat (1 - exp(-hr x)), sat = taus - g0.
             // For y = hr x small the exponential is its cubic Taylor polynomial to
             // 1e-12 relative (y <= 1e-2), so x solves x = (a0 + c2 x^2 - c3 x^3) / K
-            // with K = k + sat hr, c2 = sat hr^2 / 2, c3 = sat hr^3 / 6; each
-            // fixed-point step gains a factor y / 2, and three steps from x = a0 / K
-            // leave a relative error near 1e-11.  1 / K: an FP32 reciprocal with
-            // one FP64 Newton correction (relative error near 1e-14).
+            // with K = k + sat hr, c2 = sat hr^2 / 2, c3 = sat hr^3 / 6.  The leading
+            // term a0 / K is formed in FP64 (1 / K: an FP32 reciprocal with one FP64
+            // Newton correction, relative error near 1e-14); the correction
+            // x^2 (c2 - c3 x) / K is at most about y / 2 of x, so three fixed-point
+            // steps on it in FP32 leave a relative error below 1e-9 in x.
             const double sat = a.taus - g0;
             const double K = k + sat * hr;
-            double rK = (double)(1.0f / (float)K);
+            const float rKf = 1.0f / (float)K;
+            double rK = (double)rKf;
             rK = rK * (2.0 - K * rK);
             const double a0 = at - g0;
             xs = a0 * rK;
-            if (hr * xs <= 1e-2) {
-                const double sr = sat * rK, c2 = hr2h * sr, c3 = hr3s * sr;
-                const double x1 = xs;
+            const float x1f = (float)xs;
+            if (hr32 * x1f <= 1e-2f) {
+                const float sr = (taus32 - gres) * rKf;
+                const float c2 = hr2h * sr, c3 = hr3s * sr;
+                float d = 0.0f;
 #pragma unroll
-                for (int it = 0; it < 3; ++it) xs = x1 + xs * xs * (c2 - c3 * xs);
+                for (int it = 0; it < 3; ++it) {
+                    const float xf = x1f + d;
+                    d = xf * xf * (c2 - c3 * xf);
+                }
+                xs += (double)d;
             } else {
                 // larger slips: Newton on the FP64 residual; the step uses an FP32
                 // reciprocal of the slope (a relative step error near 1e-7 leaves
