@@ -411,6 +411,14 @@ typedef struct {
     float* g;
 } hp_cp_state;
 
+/* The single-slip return map as the plasticity kernels evaluate it, for
+ * testing: x[i] (device double[n]) = the slip of a system with resolved shear
+ * at[i] > g[i] (device float[n] each) and k[i] = P:C:P (device double[n]), the
+ * root of at - k x = g(gamma + x) for the Voce law of prm (tau0, taus, h0),
+ * x = (at - g)/k without hardening.                                          */
+HP_API int hp_debug_return_map(const hp_cp_params* prm, const float* at, const float* g, const double* k, int64_t n,
+                               double* x, void* stream);
+
 /* Zero plastic strain and slip, g = tau0.                                    */
 HP_API int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream);
 

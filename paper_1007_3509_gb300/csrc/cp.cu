@@ -79,6 +79,97 @@ __device__ __forceinline__ double exp_neg(double y) {
     return exp(-y);
 }
 
+// Constants of the single-slip return map for Voce hardening (taus, tau0, h0).
+struct RMConsts {
+    double taus, tau0, hr;  // hr = h0 / (taus - tau0); 0 without hardening
+    float taus32, hr32, hr2h, hr3s;
+    bool hard;
+};
+
+__host__ __device__ inline RMConsts rm_consts(double tau0, double taus, double h0) {
+    RMConsts c;
+    c.hard = taus - tau0 > 0.0 && h0 > 0.0;
+    c.taus = taus;
+    c.tau0 = tau0;
+    c.hr = c.hard ? h0 / (taus - tau0) : 0.0;
+    c.taus32 = (float)taus;
+    c.hr32 = (float)c.hr;
+    // series coefficients of 1 - exp(-hr x) = hr x - (hr x)^2 / 2 + (hr x)^3 / 6 - ...
+    c.hr2h = (float)(0.5 * c.hr * c.hr);
+    c.hr3s = (float)(c.hr * c.hr * c.hr / 6.0);
+    return c;
+}
+
+// Slip x >= 0 of one system with resolved shear |tau| = at > g (slip resistance
+// g, P:C:P = k): the root of f(x) = (at - g) - k x - sat (1 - exp(-hr x)),
+// sat = taus - g, i.e. |tau| - x k = g(gamma + x) for the Voce law; x = (at - g) / k
+// without hardening.  *g_new = g(gamma + x), from consistency at - k x.
+//
+// With y = hr x and q = sat hr / K (K = k + sat hr, q < 1), the exponential's
+// cubic Taylor polynomial changes x by at most q y^3 / 24 relative; where that
+// is below 4e-10 (q y^3 <= 1e-8, y <= 1e-2) x solves
+// x = (a0 + c2 x^2 - c3 x^3) / K with a0 = at - g, c2 = sat hr^2 / 2,
+// c3 = sat hr^3 / 6.  The leading term a0 / K is formed in FP64 (1 / K: an FP32
+// reciprocal with one FP64 Newton correction, relative error near 1e-14); the
+// correction x^2 (c2 - c3 x) / K is at most q y / 2 of x and each fixed-point
+// step shrinks its error by a factor q y, so three steps in FP32 leave it below
+// 1e-10.  Other slips take Newton on the exact FP64 residual.  The
+// constants come as scalars so that the inlined code keeps the kernel's own
+// registers and launch parameters.
+__device__ __forceinline__ double return_map(float at_f, float g, double k, bool hard, double taus, double tau0,
+                                             double hr, float taus32, float hr32, float hr2h, float hr3s,
+                                             float* g_new) {
+    const double g0 = g;
+    const double at = at_f;
+    double xs;
+    if (!hard) {
+        xs = (at - g0) / k;
+    } else {
+        const double sat = taus - g0;
+        const double K = k + sat * hr;
+        const float rKf = 1.0f / (float)K;
+        double rK = (double)rKf;
+        rK = rK * (2.0 - K * rK);
+        xs = (at - g0) * rK;
+        const float x1f = (float)xs;
+        const float sr = (taus32 - g) * rKf;  // sat / K
+        const float y = hr32 * x1f, q = hr32 * sr;
+        if (y <= 1e-2f && y * y * y * q <= 1e-8f) {
+            const float c2 = hr2h * sr, c3 = hr3s * sr;
+            float d = 0.0f;
+#pragma unroll
+            for (int it = 0; it < 3; ++it) {
+                const float xf = x1f + d;
+                d = xf * xf * (c2 - c3 * xf);
+            }
+            xs += (double)d;
+        } else {
+            // the step uses an FP32 reciprocal of the slope (a relative step error
+            // near 1e-7 leaves the iteration converging to the same FP64 root,
+            // tested on the exact residual)
+#pragma unroll 1
+            for (int it = 0; it < 8; ++it) {
+                const double ey = exp_neg(hr * xs);
+                const double f = at - xs * k - (taus - sat * ey);
+                if (fabs(f) < 1e-13 * tau0) break;
+                const double fp = -k - sat * hr * ey;
+                xs -= f * (double)(1.0f / (float)fp);
+            }
+        }
+    }
+    *g_new = hard ? (float)(at - k * xs) : g;
+    return xs;
+}
+
+// The return map as the plasticity kernel evaluates it, for testing.
+__global__ void k_rm_eval(const float* __restrict__ at, const float* __restrict__ g, const double* __restrict__ k,
+                          int64_t n, RMConsts c, double* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float gn;
+    if (i < n)
+        x[i] = return_map(at[i], g[i], k[i], c.hard, c.taus, c.tau0, c.hr, c.taus32, c.hr32, c.hr2h, c.hr3s, &gn);
+}
+
 template <bool STRAIN>
 __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,7 +216,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
     const bool hard = dtau > 0.0 && a.h0 > 0.0;
     const double hr = hard ? a.h0 / dtau : 0.0;
     const float hr32 = (float)hr, taus32 = (float)a.taus;
-    // series coefficients of 1 - exp(-hr x) = hr x - (hr x)^2 / 2 + (hr x)^3 / 6 - ...
+    // series coefficients of the return map
     const float hr2h = (float)(0.5 * hr * hr), hr3s = (float)(hr * hr * hr / 6.0);
     float ee[6], s[6];
     for (int32_t inc = 1; inc <= a.n_incr; ++inc) {
@@ -191,55 +282,10 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
             for (int al = 0; al < 12; ++al)
                 if (al == last) tau_pick = tau[al];
         }
-        // the single-slip return map of the chosen system, converged in FP64
-        const double g0 = gres;
-        const double at = fabs((double)tau_pick);
-        const double k = c_k[pick];
-        double xs;
-        if (!hard) {
-            xs = (at - g0) / k;
-        } else {
-            // residual f(x) = (|tau| - g0) - k x - sat (1 - exp(-hr x)), sat = taus - g0.
-            // For y = hr x small the exponential is its cubic Taylor polynomial to
-            // 1e-12 relative (y <= 1e-2), so x solves x = (a0 + c2 x^2 - c3 x^3) / K
-            // with K = k + sat hr, c2 = sat hr^2 / 2, c3 = sat hr^3 / 6.  The leading
-            // term a0 / K is formed in FP64 (1 / K: an FP32 reciprocal with one FP64
-            // Newton correction, relative error near 1e-14); the correction
-            // x^2 (c2 - c3 x) / K is at most about y / 2 of x, so three fixed-point
-            // steps on it in FP32 leave a relative error below 1e-9 in x.
-            const double sat = a.taus - g0;
-            const double K = k + sat * hr;
-            const float rKf = 1.0f / (float)K;
-            double rK = (double)rKf;
-            rK = rK * (2.0 - K * rK);
-            const double a0 = at - g0;
-            xs = a0 * rK;
-            const float x1f = (float)xs;
-            if (hr32 * x1f <= 1e-2f) {
-                const float sr = (taus32 - gres) * rKf;
-                const float c2 = hr2h * sr, c3 = hr3s * sr;
-                float d = 0.0f;
-#pragma unroll
-                for (int it = 0; it < 3; ++it) {
-                    const float xf = x1f + d;
-                    d = xf * xf * (c2 - c3 * xf);
-                }
-                xs += (double)d;
-            } else {
-                // larger slips: Newton on the FP64 residual; the step uses an FP32
-                // reciprocal of the slope (a relative step error near 1e-7 leaves
-                // the iteration converging to the same FP64 root, tested on the
-                // exact residual)
-#pragma unroll 1
-                for (int it = 0; it < 8; ++it) {
-                    const double ey = exp_neg(hr * xs);
-                    const double f = at - xs * k - (a.taus - sat * ey);
-                    if (fabs(f) < 1e-13 * a.tau0) break;
-                    const double fp = -k - sat * hr * ey;
-                    xs -= f * (double)(1.0f / (float)fp);
-                }
-            }
-        }
+        // the single-slip return map of the chosen system (FP64 where it matters)
+        float g_next;
+        const double xs = return_map(fabsf(tau_pick), gres, c_k[pick], hard, a.taus, a.tau0, hr, taus32, hr32, hr2h,
+                                     hr3s, &g_next);
         const float sg = tau_pick > 0.f ? 1.f : -1.f;
         const float m0 = c_m[pick][0], m1 = c_m[pick][1], m2 = c_m[pick][2];
         const float n0 = c_n[pick][0], n1 = c_n[pick][1], n2 = c_n[pick][2];
@@ -251,8 +297,7 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
         ep[4] += xf * 0.5f * (m0 * n2 + m2 * n0);
         ep[5] += xf * 0.5f * (m0 * n1 + m1 * n0);
         gam += (float)xs;
-        // consistency at the solved slip: g(gamma + x) = |tau| - k x
-        gres = hard ? (float)(at - k * xs) : gres;
+        gres = g_next;  // g(gamma + x) = |tau| - k x at the solved slip
     }
 #pragma unroll
     for (int v = 0; v < 6; ++v) a.eps_p[(int64_t)v * a.P + p] = ep[v];
@@ -338,6 +383,17 @@ int upload_tables(const hp_cp_params* prm) {
 }  // namespace hp
 
 using namespace hp;
+
+extern "C" int hp_debug_return_map(const hp_cp_params* prm, const float* at, const float* g, const double* k,
+                                   int64_t n, double* x, void* stream) {
+    if (!prm || !at || !g || !k || !x || n < 0) return set_error(HP_ERR_ARG, "hp_debug_return_map: bad arguments");
+    if (n == 0) return HP_OK;
+    ::hp::count_launch();
+    k_rm_eval<<<(unsigned)((n + 255) / 256), 256, 0, as_stream(stream)>>>(at, g, k, n, rm_consts(prm->tau0, prm->taus, prm->h0),
+                                                                           x);
+    HP_LAUNCH_CHECK("k_rm_eval");
+    return HP_OK;
+}
 
 extern "C" int hp_cp_reset(const hp_cp_params* prm, hp_cp_state* st, void* stream) {
     if (!prm || !st || st->P < 1 || !st->eps_p || !st->gamma || !st->g)

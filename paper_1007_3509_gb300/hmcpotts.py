@@ -135,6 +135,8 @@ _SIGS = {
     "hp_elastic_solve": ([C.POINTER(hp_cp_params), C.POINTER(hp_elastic_params), C.c_void_p, C.c_void_p, C.c_void_p,
                           C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                           C.c_void_p], C.c_int),
+    "hp_debug_return_map": ([C.POINTER(hp_cp_params), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                             C.c_void_p], C.c_int),
     "hp_det_reset": ([C.POINTER(hp_det_state), C.c_void_p], C.c_int),
     "hp_det_step": ([C.POINTER(hp_cp_params), C.c_void_p, C.c_void_p, C.c_uint32, C.c_int32,
                      C.POINTER(hp_det_state), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -439,6 +441,12 @@ def hp_cp_step_strain(prm, seed, grain, quat, t, eps_total, eps_p, gamma, g, sig
                                    _dev(eps_total, 6 * P, 4, nm + " eps_total"), C.byref(st),
                                    _dev(sigma, 6 * P, 4, nm + " sigma"), _dev(w, P, 4, nm + " w"),
                                    _dev(erho, P, 4, nm + " erho"), _dev(b, P, 4, nm + " b"), _stream(stream)))
+
+
+def hp_debug_return_map(prm, at, g, k, x, stream=None):
+    n, w = int(at.numel()), "hp_debug_return_map"
+    _check(lib().hp_debug_return_map(C.byref(prm), _dev(at, n, 4, w + " at"), _dev(g, n, 4, w + " g"),
+                                     _dev(k, n, 8, w + " k"), n, _dev(x, n, 8, w + " x"), _stream(stream)))
 
 
 def _det_state(P, eps_p, gamma, who):

@@ -207,3 +207,36 @@ def test_cp_full_size_sampled(oracle):
     rel = np.linalg.norm(s_gpu - s_ref, axis=1) / np.linalg.norm(s_ref, axis=1)
     assert near.mean() < 0.02
     assert rel[~near].max() <= 1e-5, rel[~near].max()
+
+
+def test_return_map_against_a_root_finder():
+    """The plasticity kernels' return map (a series where its truncation bound
+    q y^3 / 24 is small, y = hr x, q = sat hr / K; Newton elsewhere) against
+    scipy's brentq on the exact Voce residual in FP64, over slips spanning both
+    branches: relative error below 1e-9 (series) and 1e-11 (Newton)."""
+    torch, hm = need_gpu()
+    from scipy.optimize import brentq
+    c = dict(synth.TABLE1)
+    rng = np.random.default_rng(3)
+    n = 3000
+    g = rng.uniform(c["tau0"], 100.0, size=n).astype(np.float32)
+    at = (g.astype(np.float64) + 10 ** rng.uniform(-4, 2.3, size=n)).astype(np.float32)
+    k = rng.uniform(2e4, 8e4, size=n)
+    for h0 in (c["h0"], 5e4):
+        prm = hm.cp_params(c["C11"], c["C12"], c["C44"], c["tau0"], c["taus"], h0, c["beta"], 1e-4)
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        hm.hp_debug_return_map(prm, torch.from_numpy(at).cuda(), torch.from_numpy(g).cuda(),
+                               torch.from_numpy(k).cuda(), x)
+        torch.cuda.synchronize()
+        xg = x.cpu().numpy()
+        hr = h0 / (c["taus"] - c["tau0"])
+        branches = set()
+        for i in range(n):
+            a0, sat = float(at[i]) - float(g[i]), c["taus"] - float(g[i])
+            f = lambda v: a0 - k[i] * v - sat * (-np.expm1(-hr * v))
+            root = brentq(f, 0.0, a0 / k[i], xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=200)
+            y, q = hr * a0 / (k[i] + sat * hr), sat * hr / (k[i] + sat * hr)
+            series = y <= 1.01e-2 and q * y ** 3 <= 1.01e-8  # the kernel decides in FP32
+            branches.add(series)
+            assert abs(xg[i] - root) <= (1e-9 if series else 1e-11) * root, (h0, i, xg[i], root)
+        assert branches == {True, False}
