@@ -100,6 +100,24 @@ __host__ __device__ inline RMConsts rm_consts(double tau0, double taus, double h
     return c;
 }
 
+// Newton on the exact FP64 Voce residual at - x k - (taus - sat exp(-hr x)) from
+// x; the step uses an FP32 reciprocal of the slope (a relative step error near
+// 1e-7 leaves the iteration converging to the same FP64 root, tested on the
+// exact residual).  Not inlined: the compiler would otherwise evaluate its
+// first residual speculatively on every lane of the common (series) path.
+__device__ __noinline__ double newton_slip(double at, double k, double taus, double tau0, double hr, double sat,
+                                           double xs) {
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        const double ey = exp_neg(hr * xs);
+        const double f = at - xs * k - (taus - sat * ey);
+        if (fabs(f) < 1e-13 * tau0) break;
+        const double fp = -k - sat * hr * ey;
+        xs -= f * (double)(1.0f / (float)fp);
+    }
+    return xs;
+}
+
 // Slip x >= 0 of one system with resolved shear |tau| = at > g (slip resistance
 // g, P:C:P = k): the root of f(x) = (at - g) - k x - sat (1 - exp(-hr x)),
 // sat = taus - g, i.e. |tau| - x k = g(gamma + x) for the Voce law; x = (at - g) / k
@@ -144,17 +162,7 @@ __device__ __forceinline__ double return_map(float at_f, float g, double k, bool
             }
             xs += (double)d;
         } else {
-            // the step uses an FP32 reciprocal of the slope (a relative step error
-            // near 1e-7 leaves the iteration converging to the same FP64 root,
-            // tested on the exact residual)
-#pragma unroll 1
-            for (int it = 0; it < 8; ++it) {
-                const double ey = exp_neg(hr * xs);
-                const double f = at - xs * k - (taus - sat * ey);
-                if (fabs(f) < 1e-13 * tau0) break;
-                const double fp = -k - sat * hr * ey;
-                xs -= f * (double)(1.0f / (float)fp);
-            }
+            xs = newton_slip(at, k, taus, tau0, hr, sat, xs);
         }
     }
     *g_new = hard ? (float)(at - k * xs) : g;
