@@ -583,9 +583,15 @@ HP_API int hp_sur_generate(const hp_cp_params* prm, uint64_t seed, const float* 
  * params, m, v: device float[hp_mlp_param_count()], updated in place.  loss
  * (device float, may be NULL) receives the last minibatch loss; with
  * log_every > 0 the loss after every log_every-th step is also copied to the
- * host array loss_log[steps / log_every] (one synchronisation each).
- * Allocates its gradient buffer for the duration of the call; asynchronous
- * otherwise.                                                                  */
+ * host array loss_log[steps / log_every] (copied after the run).
+ * The whole run is one cooperative launch when every CTA of the gradient kernel
+ * can be resident (one per SM): a grid barrier separates each step's gradients
+ * from its update.  Work on other streams that keeps SMs busy can hold CTAs
+ * back; a barrier then gives up after about two seconds, the run stops early and
+ * hp_mlp_status reports HP_ERR_TIMEOUT.  When the CTAs cannot all be resident
+ * the steps run as two launches each instead (same arithmetic).  Allocates its
+ * work buffers (gradient slots, packed weights, the schedule) for the duration
+ * of the call and synchronises the stream before returning.                  */
 typedef struct {
     int32_t steps;    /* Adam steps                                           */
     int64_t batch;    /* rows per minibatch (0 = all rows)                    */
