@@ -358,6 +358,17 @@ def run_e2e(torch, hm, job, args):
     h_mp = torch.empty(N, dtype=torch.int32).pin_memory()
     job.lat.hp_get_spins(h_q, h_mp)
     torch.cuda.synchronize()
+    # The host link itself, outside the timed region: one plain pinned copy of
+    # the q array each way (h_q holds the device lattice's values, so the upload
+    # leaves the state unchanged).  The copies of a step move twice this.
+    link = {}
+    for name, dst, src in (("h2d", job.q, h_q), ("d2h", h_q, job.q)):
+        e0, e1 = _events(torch)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        link[name] = round(4 * N / (e0.elapsed_time(e1) * 1e6), 1)
     main = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
 
@@ -389,6 +400,7 @@ def run_e2e(torch, hm, job, args):
     per = statistics.mean(ms) / 1e3
     return {"value": round(N * job.every / per, 1), "unit": "site-updates/s", "h2d_bytes_per_step": 8 * N,
             "d2h_bytes_per_step": 8 * N + 24 * 8, "ms_per_step": round(per * 1e3, 3),
+            "host_link_gbs": link,
             "path": "hp_set_spins (host, copy stream) overlapping hp_cp_step, then hp_sweep; hp_get_spins (host, "
                     "copy stream) overlapping hp_measure"}
 
