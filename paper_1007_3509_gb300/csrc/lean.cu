@@ -37,16 +37,26 @@ namespace {
 __device__ int g_lean_err;
 
 // Tiled TMA descriptors of the launch's source arrays (3D, Lx x Ly x Lz int32,
-// box 64 x WY x 1); zeroed when a window is never copied by TMA.
+// box 64 x WY x 1); zeroed when a window is never copied by TMA.  `tab` maps a
+// per-material-point field table laid out like the lattice (entry p belongs to
+// the point that started at site p).
 struct alignas(64) LeanMaps {
-    CUtensorMap q_in, q_nb, mp_in, mp_nb;
-    int ok;  // 1: the descriptors are valid
+    CUtensorMap q_in, q_nb, mp_in, mp_nb, tab;
+    int ok;   // 1: the q (and mp) descriptors are valid
+    int pf;   // 1: `tab` is valid (the field table is prefetched into L2)
 };
 
 __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
+}
+
+// Bring one box of a mapped array into L2 (a hint: nothing lands in shared
+// memory and nothing is waited for).
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z) : "memory");
 }
 
 
@@ -151,6 +161,15 @@ __device__ __forceinline__ void lean_body(const PlaneArgs& a, const LeanMaps* ma
                 tma_box(s_addr(base + 3 * PS), &maps->mp_nb, xs, ys, zlo, mb);
                 tma_box(s_addr(base + 4 * PS), &maps->mp_in, xs, ys, z, mb);
                 tma_box(s_addr(base + 5 * PS), &maps->mp_nb, xs, ys, zhi, mb);
+            }
+            // The test stages look up the field of the window's material points.
+            // A point moves only a few sites under grain growth, so most of them
+            // lie in the table's boxes at the window's own coordinates: start
+            // those towards L2 now, a few thousand cycles before the lookups.
+            if (FIELD == 2 && maps->pf) {
+                tma_prefetch_l2(&maps->tab, xs, ys, zlo);
+                tma_prefetch_l2(&maps->tab, xs, ys, z);
+                tma_prefetch_l2(&maps->tab, xs, ys, zhi);
             }
         }
     } else if (vec) {
@@ -413,6 +432,10 @@ int launch_lean(const PlaneArgs& a, int planes, cudaStream_t s) {
     bool ok = a.Lx >= 64 && encode_box(&maps.q_in, a.q_in, a, WY) && encode_box(&maps.q_nb, a.q_nb, a, WY);
     if (ok && HASMP) ok = encode_box(&maps.mp_in, a.mp_in, a, WY) && encode_box(&maps.mp_nb, a.mp_nb, a, WY);
     maps.ok = ok ? 1 : 0;
+    // a per-point field table of one entry per site shares the lattice's layout
+    if (ok && FIELD == 2 && a.table_n == (uint32_t)((uint64_t)a.Lx * a.Ly * a.Lz) &&
+        (uint64_t)a.Lx * a.Ly * a.Lz <= 0xFFFFFFFFull)
+        maps.pf = encode_box(&maps.tab, a.table, a, WY) ? 1 : 0;
     count_launch();
     k_lean26<WY, FIELD, HASMP><<<dim3((unsigned)a.tiles, (unsigned)planes), Cfg::kLT, smem, s>>>(a, maps);
     HP_LAUNCH_CHECK("k_lean26");
