@@ -222,7 +222,7 @@ class Hybrid3D:
 # kernel (one plane parity, the point-field lean window), from an ncu capture of
 # that exact kernel on the bench lattice (profiles/k_lean26_3d1024_point_field.md);
 # keyed by (edge, tile variant).  None for any other kernel or lattice.
-MEASURED_TRAFFIC_3D = {}
+MEASURED_TRAFFIC_3D = {(1024, 11): 13.069e9 + 4.277e9}
 
 
 def sweep_kernel_name(nbr, variant):
