@@ -35,9 +35,31 @@ __constant__ float c_n[12][3];
 __constant__ double c_k[12];  // P:C:P per system
 __constant__ float c_kf[12];
 
+// Constants of the single-slip return map for Voce hardening (taus, tau0, h0).
+struct RMConsts {
+    double taus, tau0, hr;  // hr = h0 / (taus - tau0); 0 without hardening
+    float taus32, hr32, hr2h, hr3s;
+    bool hard;
+};
+
+__host__ __device__ inline RMConsts rm_consts(double tau0, double taus, double h0) {
+    RMConsts c;
+    c.hard = taus - tau0 > 0.0 && h0 > 0.0;
+    c.taus = taus;
+    c.tau0 = tau0;
+    c.hr = c.hard ? h0 / (taus - tau0) : 0.0;
+    c.taus32 = (float)taus;
+    c.hr32 = (float)c.hr;
+    // series coefficients of 1 - exp(-hr x) = hr x - (hr x)^2 / 2 + (hr x)^3 / 6 - ...
+    c.hr2h = (float)(0.5 * c.hr * c.hr);
+    c.hr3s = (float)(c.hr * c.hr * c.hr / 6.0);
+    return c;
+}
+
 struct CPArgs {
     float C11, C12, C44;
     double tau0, taus, h0;
+    RMConsts rm;  // rm_consts(tau0, taus, h0), once per launch on the host
     float beta;
     float G;
     float e;
@@ -77,27 +99,6 @@ __device__ __forceinline__ double exp_neg(double y) {
         return 1.0 - y * (1.0 - y * (0.5 - y * (1.0 / 6.0 - y * (1.0 / 24.0 - y * (1.0 / 120.0 - y * (1.0 / 720.0))))));
     }
     return exp(-y);
-}
-
-// Constants of the single-slip return map for Voce hardening (taus, tau0, h0).
-struct RMConsts {
-    double taus, tau0, hr;  // hr = h0 / (taus - tau0); 0 without hardening
-    float taus32, hr32, hr2h, hr3s;
-    bool hard;
-};
-
-__host__ __device__ inline RMConsts rm_consts(double tau0, double taus, double h0) {
-    RMConsts c;
-    c.hard = taus - tau0 > 0.0 && h0 > 0.0;
-    c.taus = taus;
-    c.tau0 = tau0;
-    c.hr = c.hard ? h0 / (taus - tau0) : 0.0;
-    c.taus32 = (float)taus;
-    c.hr32 = (float)c.hr;
-    // series coefficients of 1 - exp(-hr x) = hr x - (hr x)^2 / 2 + (hr x)^3 / 6 - ...
-    c.hr2h = (float)(0.5 * c.hr * c.hr);
-    c.hr3s = (float)(c.hr * c.hr * c.hr / 6.0);
-    return c;
 }
 
 // Newton on the exact FP64 Voce residual at - x k - (taus - sat exp(-hr x)) from
@@ -220,12 +221,12 @@ __global__ void __launch_bounds__(kT) k_cp(CPArgs a) {
     for (int v = 0; v < 6; ++v) ep[v] = a.eps_p[(int64_t)v * a.P + p];
     float gam = a.gamma[p];
     float gres = a.g[p];
-    const double dtau = a.taus - a.tau0;
-    const bool hard = dtau > 0.0 && a.h0 > 0.0;
-    const double hr = hard ? a.h0 / dtau : 0.0;
-    const float hr32 = (float)hr, taus32 = (float)a.taus;
-    // series coefficients of the return map
-    const float hr2h = (float)(0.5 * hr * hr), hr3s = (float)(hr * hr * hr / 6.0);
+    // the return map's constants (two FP64 divisions among them) come from the
+    // host: per thread they cost about as much FP64 work as the two increments
+    const bool hard = a.rm.hard;
+    const double hr = a.rm.hr;
+    const float hr32 = a.rm.hr32, taus32 = a.rm.taus32;
+    const float hr2h = a.rm.hr2h, hr3s = a.rm.hr3s;
     float ee[6], s[6];
     for (int32_t inc = 1; inc <= a.n_incr; ++inc) {
         const uint32_t t = a.t0 + (uint32_t)inc;
@@ -426,6 +427,7 @@ extern "C" int hp_cp_step(const hp_cp_params* prm, uint64_t seed, const int32_t*
     CPArgs a;
     a.C11 = (float)prm->C11; a.C12 = (float)prm->C12; a.C44 = (float)prm->C44;
     a.tau0 = prm->tau0; a.taus = prm->taus; a.h0 = prm->h0;
+    a.rm = rm_consts(prm->tau0, prm->taus, prm->h0);
     a.beta = (float)prm->beta; a.G = (float)prm->G; a.e = (float)prm->e_incr; a.scale = (float)prm->energy_scale;
     a.w_weight = (float)prm->w_weight;
     a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t0; a.n_incr = n_incr; a.P = st->P;
@@ -451,6 +453,7 @@ extern "C" int hp_cp_step_strain(const hp_cp_params* prm, uint64_t seed, const i
     CPArgs a;
     a.C11 = (float)prm->C11; a.C12 = (float)prm->C12; a.C44 = (float)prm->C44;
     a.tau0 = prm->tau0; a.taus = prm->taus; a.h0 = prm->h0;
+    a.rm = rm_consts(prm->tau0, prm->taus, prm->h0);
     a.beta = (float)prm->beta; a.G = (float)prm->G; a.e = (float)prm->e_incr; a.scale = (float)prm->energy_scale;
     a.w_weight = (float)prm->w_weight;
     a.seed = seed; a.grain = grain; a.quat = quat; a.t0 = t - 1; a.n_incr = 1; a.P = st->P;
